@@ -1,0 +1,208 @@
+/*
+ * lmep.h -- C ABI of the GB300 (sm_103a) Local Matrix Exponential Propagator.
+ *
+ * Method: V. Bayona, "Unifying Finite Differences and Semi-Lagrangian Schemes
+ * via Localized Matrix Exponentials".  For every grid point x_i the library
+ *   (a1) selects the point's stencil window and harvest row       (Sec. 2.1 steps 1, 3)
+ *   (a2) builds the derivative matrices D^(k) on the window        (Sec. 2.1 step 1, Fornberg)
+ *   (a3) assembles X_i = dt A_i, A_i = c0 I + c1 D1 + c2 D2 + c3 D3 - frozen_adv u_i D1
+ *                                                                    (Thm. 2 proof)
+ *   (a4) exponentiates X_i, or the augmented local matrix for the
+ *        ETD phi-functions                                           (Sec. 2.1 step 2, Sec. 3.1)
+ *   (a5) harvests the weight rows                                    (Sec. 2.1 step 3, Sec. 3.1 step 2)
+ *   (a6) applies them as one banded update u <- W u + dt Phi N(u)   (Sec. 3, Sec. 3.1 step 3)
+ * and (a7) runs the discrete adjoint of the frozen-velocity step.
+ *
+ * Conventions (all entry points):
+ *  - Every pointer named *_dev is device memory on the current CUDA device,
+ *    owned by the caller, contiguous, at least 16-byte aligned.  *_host is
+ *    host memory.  The library owns only the handle and its status block.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  No call synchronises except
+ *    lmep_sync_status and lmep_fma_peak.
+ *  - Invalid arguments return LMEP_ERR_INVALID before anything is launched.
+ *    A failed launch returns LMEP_ERR_CUDA.  Non-finite results produced on
+ *    the device are flagged and reported by the next lmep_sync_status.
+ *  - Nothing throws across the ABI.  A handle is not thread-safe.
+ *  - Floating-point layouts: dtype follows `precision`: LMEP_PREC_FP64 uses
+ *    double everywhere; LMEP_PREC_MIXED (the batched FP32 form) stores the
+ *    state and the weights as float, evaluates the Pade polynomial products
+ *    in FP32 with FP32 accumulation, and keeps the Pade denominator solve and
+ *    the squaring phase in FP64.
+ */
+#ifndef LMEP_H
+#define LMEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LMEP_API __attribute__((visibility("default")))
+#else
+#define LMEP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LMEP_OK = 0,
+  LMEP_ERR_INVALID = 1,     /* bad argument; nothing was launched */
+  LMEP_ERR_CUDA = 2,        /* a CUDA call failed; see lmep_last_error() */
+  LMEP_ERR_NONFINITE = 3,   /* a kernel produced Inf/NaN since the last sync */
+  LMEP_ERR_TIMEOUT = 4,     /* reserved: no kernel of this library waits on a flag */
+  LMEP_ERR_UNSUPPORTED = 5, /* valid request outside the built shapes (e.g. n + n_phi > 16) */
+  LMEP_ERR_NOMEM = 6        /* workspace smaller than required */
+} lmep_status;
+
+typedef enum { LMEP_BC_PERIODIC = 0, LMEP_BC_DIRICHLET = 1, LMEP_BC_NEUMANN = 2 } lmep_bc;
+typedef enum { LMEP_PREC_FP64 = 0, LMEP_PREC_MIXED = 1 } lmep_precision;
+typedef enum { LMEP_SCHEME_LINEAR = 0, LMEP_SCHEME_ETD1 = 1, LMEP_SCHEME_ETDRK2 = 2 } lmep_scheme;
+typedef enum { LMEP_N_NONE = 0, LMEP_N_ALLEN_CAHN = 1, LMEP_N_KDV = 2 } lmep_nonlin;
+
+/* Uniform 1-D grid and stencil (Sec. 2.1 step 1).
+ *  N      number of points.  Periodic: x_j = x0 + j h, j < N.  Dirichlet and
+ *         Neumann: both walls are grid points (x_0 and x_{N-1}).
+ *  h      spacing.
+ *  bc     lmep_bc.  Dirichlet walls keep bc_lo / bc_hi and are never updated;
+ *         near a wall the window slides inside the domain (one-sided
+ *         stencil, edge row).  Neumann: homogeneous, even reflection about the
+ *         wall node.  Periodic: centred window, indices mod N.
+ *  n      stencil width, odd, 3 <= n <= 15, n <= N.
+ *  departure_centring  frozen-velocity problems only: shift each window
+ *         upstream by k_i = clamp(floor(u_i dt / h + 1/2), -(n-1)/2, (n-1)/2). */
+typedef struct lmep_grid {
+  int64_t N;
+  double h;
+  int32_t bc;
+  int32_t n;
+  int32_t departure_centring;
+  int32_t reserved0;
+  double bc_lo, bc_hi;
+} lmep_grid;
+
+/* Linear operator L = c0 + c1 d/dx + c2 d^2/dx^2 + c3 d^3/dx^3 (Thm. 2 proof),
+ * plus -frozen_adv * u_i * d/dx at point i with u_i frozen (local Burgers). */
+typedef struct lmep_operator {
+  double c0, c1, c2, c3;
+  double frozen_adv;
+} lmep_operator;
+
+typedef struct lmep_handle lmep_handle;
+
+/* Create a handle on the current device.  Allocates the device status block
+ * (one cudaMalloc of 256 bytes); *out receives the handle. */
+LMEP_API lmep_status lmep_create(lmep_handle** out);
+LMEP_API lmep_status lmep_destroy(lmep_handle* h);
+
+/* (a1)-(a3): for points i0 .. i0+count-1 write, on the device,
+ *   start_dev[p] window start (global index of window node 0 before any
+ *                wrap or reflection), row_dev[p] the harvest row r,
+ *   M_dev[p]     the d x d row-major matrix that (a4) exponentiates, d = n + n_phi:
+ *                n_phi = 0: X = dt A_i (plain, not re-centred);
+ *                n_phi > 0: the transposed row-restricted augmented matrix
+ *                [[X, 0], [dt e_r^T, 0], [0, dt, 0]..] whose rows r, n, n+1, ..
+ *                (first n columns) are row r of exp(X), dt phi_1(X), dt^2 phi_2(X), ..
+ * u_dev: double[N] frozen velocities, required iff op->frozen_adv != 0.
+ * Sizes: M_dev double[count][d][d]; start_dev, row_dev int32[count]. */
+LMEP_API lmep_status lmep_build_operator(lmep_handle* h, const lmep_grid* g, const lmep_operator* op,
+                                double dt, int32_t n_phi, const double* u_dev, int64_t i0,
+                                int64_t count, double* M_dev, int32_t* start_dev,
+                                int32_t* row_dev, void* stream);
+
+/* (a4) alone: E_p = exp(A_p) for P matrices of size d x d (3 <= d <= 16),
+ * row-major double in and out, by Pade scaling and squaring (Higham 2005).
+ * precision LMEP_PREC_MIXED evaluates the polynomial products in FP32.
+ * ms_dev (nullable) receives int32[P][2] = (Pade degree m, squarings s). */
+LMEP_API lmep_status lmep_expm(lmep_handle* h, const double* A_dev, int64_t P, int32_t d, double* E_dev,
+                      int32_t precision, int32_t* ms_dev, void* stream);
+
+/* (a1)-(a5): harvest weight rows.
+ *  u_frozen_dev == NULL: constant coefficients; W_dev receives [n][1+n_phi][n]:
+ *      W[r][k][:] = row r of dt^k phi_k(dt L) (k = 0: exp(dt L)) for every row class r.
+ *  u_frozen_dev != NULL: frozen velocity (requires n_phi == 0): W_dev receives
+ *      [N][1][n], the weights of point i on its own window (zeros at Dirichlet walls).
+ *      u_frozen_dev has the state dtype of `precision`.
+ * W dtype: double for LMEP_PREC_FP64, float for LMEP_PREC_MIXED. */
+LMEP_API lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_operator* op,
+                                 double dt, int32_t n_phi, const void* u_frozen_dev, void* W_dev,
+                                 int32_t precision, void* stream);
+
+/* (a6) `nsteps` time steps of u in place (Sec. 3, Sec. 3.1 step 3).
+ *  W_dev != NULL: stored constant-coefficient weights [n][1+n_phi][n] from
+ *      lmep_harvest_weights with n_phi equal to the scheme (0 linear, 1 ETD1, 2 ETDRK2).
+ *      Linear:  u+ = W0 u.   ETD1: u+ = W0 u + W1 N(u).
+ *      ETDRK2:  a = W0 u + W1 N(u);  u+ = a + (W2 / dt)(N(a) - N(u)).
+ *      N: Allen-Cahn u - u^3; KdV -6 u (D1 u) with D1 the harvest row of the
+ *      first-derivative matrix on the same window.
+ *  W_dev == NULL: frozen velocity: every point rebuilds and exponentiates its
+ *      own operator every step ((a1)-(a6) fused); requires the linear scheme.
+ *  u_dev, work_dev: state dtype of `precision`, N elements each; work_dev is
+ *  scratch of the same size; the result is left in u_dev. */
+LMEP_API lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, int32_t scheme,
+                      int32_t nonlin, double dt, const void* W_dev, void* u_dev, void* work_dev,
+                      int64_t nsteps, int32_t precision, void* stream);
+
+/* Many independent constant-coefficient instances advanced by one persistent
+ * launch per step (Allen-Cahn batch).  Instances share n, scheme, nonlin,
+ * dt, the operator and precision; each has its own N_b, h_b and bc_b (periodic
+ * or Neumann).  The caller allocates a workspace of lmep_batch_workspace_bytes
+ * bytes; lmep_batch_prepare fills it (tile table and per-instance weights,
+ * harvested on the device) and must run before lmep_step_batched.  State u is
+ * the concatenation of all instances (offsets = exclusive prefix sum of N_b). */
+typedef struct lmep_batch_desc {
+  int64_t B;                 /* number of instances */
+  const int64_t* N_host;     /* [B] points per instance */
+  const double* h_host;      /* [B] spacing per instance */
+  const int32_t* bc_host;    /* [B] LMEP_BC_PERIODIC or LMEP_BC_NEUMANN */
+  int32_t n;                 /* stencil width (odd, <= 13 for ETDRK2) */
+  int32_t scheme;            /* lmep_scheme */
+  int32_t nonlin;            /* lmep_nonlin (KdV not supported in batches) */
+  int32_t tile;              /* points per tile: 0 = default; else a multiple of 256 */
+  int32_t block;             /* threads per CTA: 0 = default; 128, 256 or 512 */
+  int32_t ctas_per_sm;       /* persistent CTAs per SM: 0 = default */
+  double dt;
+  lmep_operator op;          /* shared coefficients (frozen_adv must be 0) */
+} lmep_batch_desc;
+
+LMEP_API lmep_status lmep_batch_workspace_bytes(const lmep_batch_desc* d, int32_t precision,
+                                       size_t* bytes_out);
+LMEP_API lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* workspace_dev,
+                               size_t workspace_bytes, int32_t precision, void* stream);
+LMEP_API lmep_status lmep_step_batched(lmep_handle* h, const void* workspace_dev, void* u_dev,
+                              void* work_dev, int64_t nsteps, void* stream);
+
+/* (a7) one reverse step of the frozen-velocity linear scheme (Dirichlet or
+ * periodic), given the forward state u^n:
+ *   lam_dev[k]  = sum_i lam_next[i] dF_i/du_k,
+ *   *dnu_dev   += sum_i lam_next[i] dF_i/dnu   (double accumulator, nu = c2),
+ * with dF_i/du_i containing the row of the Frechet derivative of the local
+ * exponential in the direction dX/du_i = -dt frozen_adv D1, and dF_i/dnu the
+ * one in the direction dX/dnu = dt D2 (Higham, Functions of Matrices, Thm 3.6).
+ * scratch_dev: at least lmep_adjoint_scratch_bytes(g, precision) bytes.
+ * u_dev, lam_next_dev, lam_dev: state dtype; dnu_dev: double[1]. */
+LMEP_API lmep_status lmep_adjoint_scratch_bytes(const lmep_grid* g, int32_t precision, size_t* bytes_out);
+LMEP_API lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                              const void* u_dev, const void* lam_next_dev, void* lam_dev,
+                              double* dnu_dev, void* scratch_dev, size_t scratch_bytes,
+                              int32_t precision, void* stream);
+
+/* Synchronise `stream`, read and clear the device status flags.
+ * Returns LMEP_ERR_NONFINITE if any kernel produced Inf/NaN since the last call. */
+LMEP_API lmep_status lmep_sync_status(lmep_handle* h, void* stream);
+
+/* FMA-chain microbenchmark (all SMs): *flops_out receives achieved FLOP/s
+ * (2 per FMA) of FP64 (precision 0) or FP32 (precision 1) FMAs.  Synchronous. */
+LMEP_API lmep_status lmep_fma_peak(int32_t precision, double* flops_out);
+
+LMEP_API const char* lmep_status_string(lmep_status s);
+/* Thread-local text of the last error raised on this thread ("" if none). */
+LMEP_API const char* lmep_last_error(void);
+/* Library version string. */
+LMEP_API const char* lmep_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMEP_H */

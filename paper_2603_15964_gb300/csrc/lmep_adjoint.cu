@@ -1,0 +1,370 @@
+// lmep_adjoint.cu -- step (a7): one reverse step of the frozen-velocity scheme.
+//
+// Forward (per updated point i): u+_i = w_i . u[window_i], w_i = row r_i of
+// exp(X_i), X_i = dt (c0 + c1 D1 + c2 D2 + c3 D3 - fa u_i D1).  The paper has
+// no adjoint; this is the exact transpose of the step's linearisation:
+//   lam_k  = sum_i lam+_i w_i[k - start_i]  +  lam+_k (dw_k/du_k . u[window_k])
+//   dJ/dnu += sum_i lam+_i (dw_i/dnu . u[window_i]).
+// dw/du_i and dw/dnu are rows of the Frechet derivative L(X, E) of the
+// matrix exponential in the directions E = -dt fa/h Dh1 and E = dt/h^2 Dh2
+// (Higham, Functions of Matrices, 2008, Sec. 3.2).  L is obtained by
+// differentiating every step of Pade-13 scaling and squaring with the
+// product rule (the approach of Al-Mohy & Higham, SIMAX 30(4), 2009):
+//   powers  A_2k and their derivatives M_2k,
+//   U, V and L_U, L_V,
+//   R = Q^-1 P and L = Q^-1 [(L_U + L_V) + (L_U - L_V) R],
+//   squaring  L <- R L + L R,  R <- R^2.
+// Everything in this file runs in FP64; lam is stored in the state dtype.
+// The exact re-centring of the forward step (row r of exp(X) equals row r-k
+// of exp(X + k Dh1)) shifts X by a constant matrix, so the directions E are
+// unchanged and the same identity holds for L.
+#include <cstdio>
+
+#include "lmep_device.cuh"
+#include "lmep_internal.h"
+
+namespace lmep {
+
+namespace {
+
+constexpr int AW = 2;                      // warps per CTA
+constexpr int DHB = 3 * DMAX * LD * 8;     // Dh1..Dh3 bytes
+constexpr int MATB = DMAX * LD * 8;        // one d x d double matrix
+constexpr int NMAT = 20;                   // matrices per warp
+constexpr int GJB = DMAX * (6 * DMAX + 1) * 8;
+constexpr int WSB = NMAT * MATB + GJB;
+
+template <int D>
+__device__ __forceinline__ void mm(const double* A, const double* B, double* C, int lane, double beta = 0.0) {
+  for (int e = lane; e < D * D; e += 32) {
+    const int i = e / D, j = e - (e / D) * D;
+    double acc = beta == 0.0 ? 0.0 : beta * C[i * LD + j];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc = fma(A[i * LD + k], B[k * LD + j], acc);
+    C[i * LD + j] = acc;
+  }
+  __syncwarp();
+}
+
+// C = a0 M0 + a1 M1 + a2 M2 + cI I   (any Mi may be null)
+template <int D>
+__device__ __forceinline__ void lc(double* C, double a0, const double* M0, double a1, const double* M1,
+                                   double a2, const double* M2, double cI, int lane) {
+  for (int e = lane; e < D * D; e += 32) {
+    const int i = e / D, j = e - (e / D) * D, o = i * LD + j;
+    double x = (i == j) ? cI : 0.0;
+    if (M0) x = fma(a0, M0[o], x);
+    if (M1) x = fma(a1, M1[o], x);
+    if (M2) x = fma(a2, M2[o], x);
+    C[o] = x;
+  }
+  __syncwarp();
+}
+
+// Gauss-Jordan with partial pivoting on G = [Q | B1 | ... | B_nb] (stride 6*DMAX+1).
+template <int D>
+__device__ void gj_multi(double* G, int nb, int lane) {
+  const int ldg = 6 * DMAX + 1;
+  const int W = D * (1 + nb);
+  auto col = [&](int c) { return c < D ? c : DMAX + (c - D) / D * DMAX + (c - D) % D; };
+  (void)col;
+  for (int k = 0; k < D; ++k) {
+    long long key = -1;
+    int idx = k;
+    if (lane >= k && lane < D) {
+      key = __double_as_longlong(G[lane * ldg + k]) & 0x7fffffffffffffffll;
+      idx = lane;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const long long ok = __shfl_xor_sync(FULL, key, o);
+      const int oi = __shfl_xor_sync(FULL, idx, o);
+      if (ok > key || (ok == key && oi < idx)) {
+        key = ok;
+        idx = oi;
+      }
+    }
+    if (idx != k) {
+      for (int c = lane; c < W; c += 32) {
+        const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
+        const double t = G[k * ldg + j];
+        G[k * ldg + j] = G[idx * ldg + j];
+        G[idx * ldg + j] = t;
+      }
+    }
+    __syncwarp();
+    const double inv = 1.0 / G[k * ldg + k];
+    for (int c = k + 1 + lane; c < W; c += 32) {
+      const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
+      G[k * ldg + j] *= inv;
+    }
+    __syncwarp();
+    const int nc = W - k - 1;
+    for (int e = lane; e < (D - 1) * nc; e += 32) {
+      const int ii = e / nc, cc = e - (e / nc) * nc;
+      const int i = ii + (ii >= k ? 1 : 0);
+      const int c = k + 1 + cc;
+      const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
+      G[i * ldg + j] = fma(-G[i * ldg + k], G[k * ldg + j], G[i * ldg + j]);
+    }
+    __syncwarp();
+  }
+}
+
+template <int D, typename ST>
+__global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST* __restrict__ u,
+                                                            const ST* __restrict__ lam_next, ST* __restrict__ Wout,
+                                                            ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
+                                                            double* dnu) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* Dh = reinterpret_cast<double*>(smem);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* base = reinterpret_cast<double*>(smem + DHB + warp * WSB);
+  auto Mt = [&](int q) { return base + q * DMAX * LD; };
+  double* X = Mt(0);
+  double* A2 = Mt(1);
+  double* A4 = Mt(2);
+  double* A6 = Mt(3);
+  double* W1 = Mt(4);
+  double* Z1 = Mt(5);
+  double* Wm = Mt(6);   // W = A6 W1 + W2, later R
+  double* T = Mt(7);
+  double* E[2] = {Mt(8), Mt(9)};
+  double* M2[2] = {Mt(10), Mt(11)};
+  double* M4[2] = {Mt(12), Mt(13)};
+  double* M6[2] = {Mt(14), Mt(15)};
+  double* LU[2] = {Mt(16), Mt(17)};
+  double* LV[2] = {Mt(18), Mt(19)};
+  double* G = base + NMAT * DMAX * LD;
+  const int ldg = 6 * DMAX + 1;
+  __shared__ double dnu_blk;
+  if (threadIdx.x == 0) dnu_blk = 0.0;
+  fornberg_block(Dh, p.n);
+  __syncthreads();
+  const int n = p.n;
+  const bool dir = p.bc == BC_DIRICHLET;
+  constexpr double b13 = pade_b(13, 13), b12 = pade_b(13, 12), b11 = pade_b(13, 11), b10 = pade_b(13, 10),
+                   b9 = pade_b(13, 9), b8 = pade_b(13, 8), b7 = pade_b(13, 7), b6 = pade_b(13, 6),
+                   b5 = pade_b(13, 5), b4 = pade_b(13, 4), b3 = pade_b(13, 3), b2 = pade_b(13, 2),
+                   b1 = pade_b(13, 1), b0 = pade_b(13, 0);
+  double dnu_acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * AW + warp; i < p.N; i += int64_t(gridDim.x) * AW) {
+    if (dir && (i == 0 || i == p.N - 1)) {
+      for (int j = lane; j < n; j += 32) Wout[i * n + j] = ST(0);
+      if (lane == 0) {
+        gu_out[i] = ST(0);
+        st_out[i] = 0;
+      }
+      continue;
+    }
+    const double ui = double(u[i]);
+    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n) : 0;
+    const int64_t st = window_start(i, p.N, n, p.bc, k);
+    const int r = int(i - st);
+    const double a1 = p.c1 - p.fa * ui;
+    const int kr = recentring_shift(a1, p.dt, p.h, n, r);
+    const int hr = r - kr;
+    // X (re-centred) and the two directions
+    const double c1h = p.dt * a1 / p.h + double(kr);
+    const double c2h = p.dt * p.c2 / (p.h * p.h), c3h = p.dt * p.c3 / (p.h * p.h * p.h);
+    for (int e = lane; e < D * D; e += 32) {
+      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
+      double x = c1h * Dh[o];
+      x = fma(c2h, Dh[DMAX * LD + o], x);
+      if (c3h != 0.0) x = fma(c3h, Dh[2 * DMAX * LD + o], x);
+      if (a == b) x += p.dt * p.c0;
+      X[o] = x;
+      E[0][o] = -(p.dt * p.fa / p.h) * Dh[o];
+      E[1][o] = (p.dt / (p.h * p.h)) * Dh[DMAX * LD + o];
+    }
+    __syncwarp();
+    double cs = 0.0;
+    if (lane < D)
+      for (int a = 0; a < D; ++a) cs += fabs(X[a * LD + lane]);
+    const double nrm = warp_max(cs);
+    int s = 0;
+    {
+      double t = nrm;
+      while (t > THETA13 && s < 1023) { t *= 0.5; ++s; }
+    }
+    const double sc = ldexp(1.0, -s);
+    for (int e = lane; e < D * D; e += 32) {
+      const int o = (e / D) * LD + e % D;
+      X[o] *= sc;
+      E[0][o] *= sc;
+      E[1][o] *= sc;
+    }
+    __syncwarp();
+    mm<D>(X, X, A2, lane);
+    mm<D>(A2, A2, A4, lane);
+    mm<D>(A4, A2, A6, lane);
+    for (int q = 0; q < 2; ++q) {
+      mm<D>(X, E[q], M2[q], lane);
+      mm<D>(E[q], X, M2[q], lane, 1.0);
+      mm<D>(A2, M2[q], M4[q], lane);
+      mm<D>(M2[q], A2, M4[q], lane, 1.0);
+      mm<D>(A4, M2[q], M6[q], lane);
+      mm<D>(M4[q], A2, M6[q], lane, 1.0);
+    }
+    lc<D>(W1, b13, A6, b11, A4, b9, A2, 0.0, lane);
+    lc<D>(Z1, b12, A6, b10, A4, b8, A2, 0.0, lane);
+    lc<D>(Wm, b7, A6, b5, A4, b3, A2, b1, lane);      // W2
+    mm<D>(A6, W1, Wm, lane, 1.0);                      // W = A6 W1 + W2
+    // derivatives: LW = A6 LW1 + M6 W1 + LW2 ; LU = X LW + E W ; LV = A6 LZ1 + M6 Z1 + LZ2
+    for (int q = 0; q < 2; ++q) {
+      lc<D>(T, b13, M6[q], b11, M4[q], b9, M2[q], 0.0, lane);          // LW1
+      lc<D>(LV[q], b7, M6[q], b5, M4[q], b3, M2[q], 0.0, lane);         // LW2 (temporarily in LV)
+      mm<D>(A6, T, LV[q], lane, 1.0);
+      mm<D>(M6[q], W1, LV[q], lane, 1.0);                               // LW
+      mm<D>(X, LV[q], LU[q], lane);
+      mm<D>(E[q], Wm, LU[q], lane, 1.0);                                // LU
+      lc<D>(T, b12, M6[q], b10, M4[q], b8, M2[q], 0.0, lane);           // LZ1
+      lc<D>(LV[q], b6, M6[q], b4, M4[q], b2, M2[q], 0.0, lane);         // LZ2
+      mm<D>(A6, T, LV[q], lane, 1.0);
+      mm<D>(M6[q], Z1, LV[q], lane, 1.0);                               // LV
+    }
+    // U = X W (into T), V = A6 Z1 + Z2 (into W1)
+    mm<D>(X, Wm, T, lane);
+    lc<D>(W1, b6, A6, b4, A4, b2, A2, b0, lane);
+    mm<D>(A6, Z1, W1, lane, 1.0);
+    // G = [V-U | V+U | LU+LV (u) | LU-LV (u) | LU+LV (nu) | LU-LV (nu)]
+    for (int e = lane; e < D * D; e += 32) {
+      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
+      const double Uv = T[o], Vv = W1[o];
+      G[a * ldg + b] = Vv - Uv;
+      G[a * ldg + DMAX + b] = Vv + Uv;
+      for (int q = 0; q < 2; ++q) {
+        G[a * ldg + (2 + 2 * q) * DMAX + b] = LU[q][o] + LV[q][o];
+        G[a * ldg + (3 + 2 * q) * DMAX + b] = LU[q][o] - LV[q][o];
+      }
+    }
+    __syncwarp();
+    gj_multi<D>(G, 5, lane);
+    // R into Wm, L_q = Y1 + Y2 R into LU[q]
+    double* R = Wm;
+    for (int e = lane; e < D * D; e += 32) {
+      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
+      R[o] = G[a * ldg + DMAX + b];
+      for (int q = 0; q < 2; ++q) {
+        LU[q][o] = G[a * ldg + (2 + 2 * q) * DMAX + b];
+        LV[q][o] = G[a * ldg + (3 + 2 * q) * DMAX + b];
+      }
+    }
+    __syncwarp();
+    for (int q = 0; q < 2; ++q) mm<D>(LV[q], R, LU[q], lane, 1.0);
+    // squaring: L <- R L + L R ; R <- R R
+    for (int t = 0; t < s; ++t) {
+      for (int q = 0; q < 2; ++q) {
+        mm<D>(R, LU[q], LV[q], lane);
+        mm<D>(LU[q], R, LV[q], lane, 1.0);
+        double* sw = LU[q];
+        LU[q] = LV[q];
+        LV[q] = sw;
+      }
+      mm<D>(R, R, T, lane);
+      double* sw = R;
+      R = T;
+      T = sw;
+    }
+    // outputs: w = R[hr], g_q = L_q[hr] . u[window]
+    double uj = 0.0;
+    if (lane < n) uj = double(u[grid_index(st + lane, p.N, p.bc)]);
+    const double gu = warp_sum(lane < n ? LU[0][hr * LD + lane] * uj : 0.0);
+    const double gn = warp_sum(lane < n ? LU[1][hr * LD + lane] * uj : 0.0);
+    if (lane < n) Wout[i * n + lane] = ST(R[hr * LD + lane]);
+    if (lane == 0) {
+      gu_out[i] = ST(gu);
+      st_out[i] = int32_t(st - i);
+      dnu_acc += double(lam_next[i]) * gn;
+    }
+    __syncwarp();
+  }
+  if (lane == 0 && dnu_acc != 0.0) atomicAdd(&dnu_blk, dnu_acc);
+  __syncthreads();
+  if (threadIdx.x == 0 && dnu_blk != 0.0) atomicAdd(dnu, dnu_blk);
+}
+
+// lam[k] = sum over points i whose window holds k of lam+_i w_i[k - start_i] + lam+_k g_u,k
+template <typename ST>
+__global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, const ST* __restrict__ W,
+                                 const ST* __restrict__ gu, const int32_t* __restrict__ st_rel,
+                                 ST* __restrict__ lam, unsigned* flags) {
+  const int n = p.n;
+  const bool dir = p.bc == BC_DIRICHLET;
+  unsigned bad = 0;
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < p.N; k += int64_t(gridDim.x) * blockDim.x) {
+    ST acc = ST(0);
+    for (int d = -(n - 1); d <= n - 1; ++d) {
+      int64_t i = k + d;
+      if (dir) {
+        if (i < 1 || i > p.N - 2) continue;
+      } else {
+        i = grid_index(i, p.N, BC_PERIODIC);
+      }
+      const int64_t sti = i + st_rel[i];
+      int64_t j = k - sti;
+      if (!dir) j = grid_index(j, p.N, BC_PERIODIC);
+      if (j >= 0 && j < n) acc = fma(lam_next[i], W[i * n + j], acc);
+    }
+    if (!dir || (k >= 1 && k <= p.N - 2)) acc = fma(lam_next[k], gu[k], acc);
+    lam[k] = acc;
+    bad |= !isfinite(double(acc));
+  }
+  if (bad) atomicOr(flags, 1u);
+}
+
+template <int D, typename ST>
+cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
+                        void* scratch, unsigned* flags, cudaStream_t s) {
+  ST* W = static_cast<ST*>(scratch);
+  ST* gu = W + p.N * p.n;
+  int32_t* st = reinterpret_cast<int32_t*>(gu + p.N);
+  const size_t smem = DHB + AW * WSB;
+  auto k1 = k_adjoint_points<D, ST>;
+  cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32 * AW, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = int64_t(device_info().sms) * per_sm;
+  const int64_t need = (p.N + AW - 1) / AW;
+  if (need < grid) grid = need;
+  k1<<<int(grid), 32 * AW, smem, s>>>(p, static_cast<const ST*>(u), static_cast<const ST*>(lam_next), W, gu, st,
+                                      dnu);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int blk = 256;
+  int64_t g2 = (p.N + blk - 1) / blk;
+  if (g2 > int64_t(device_info().sms) * 16) g2 = int64_t(device_info().sms) * 16;
+  k_adjoint_gather<ST><<<int(g2), blk, 0, s>>>(p, static_cast<const ST*>(lam_next), W, gu, st, static_cast<ST*>(lam),
+                                              flags);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed) {
+  const size_t es = mixed ? 4 : 8;
+  return size_t(N) * size_t(n + 1) * es + size_t(N) * 4 + 256;
+}
+
+cudaError_t launch_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
+                           void* scratch, bool mixed, unsigned* flags, cudaStream_t s) {
+#define ADJ_CASE(DD)                                                                              \
+  case DD:                                                                                        \
+    return mixed ? run_adjoint<DD, float>(p, u, lam_next, lam, dnu, scratch, flags, s)            \
+                 : run_adjoint<DD, double>(p, u, lam_next, lam, dnu, scratch, flags, s);
+  switch (p.n) {
+    ADJ_CASE(3)
+    ADJ_CASE(5)
+    ADJ_CASE(7)
+    ADJ_CASE(9)
+    ADJ_CASE(11)
+    ADJ_CASE(13)
+    ADJ_CASE(15)
+    default: return cudaErrorInvalidValue;
+  }
+#undef ADJ_CASE
+}
+
+}  // namespace lmep

@@ -1,0 +1,444 @@
+// lmep_api.cu -- the C ABI of include/lmep.h: argument checks, dispatch,
+// status flags and the batch workspace.  All compute runs in the kernels of
+// lmep_expm.cu, lmep_apply.cu and lmep_adjoint.cu.
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/lmep.h"
+#include "lmep_internal.h"
+
+using lmep::ApplyParams;
+using lmep::Instance;
+using lmep::KParams;
+
+struct BatchPlan {
+  ApplyParams ap;
+  const void* W;     // per-instance weights inside the workspace
+  int64_t points;    // total points of the batch
+  int grid, block;
+  bool mixed;
+  size_t bytes;
+};
+
+struct lmep_handle {
+  int device;
+  unsigned* flags;  // device status word: bit 0 = non-finite output
+  std::map<const void*, BatchPlan> plans;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lmep_status fail(lmep_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+lmep_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(LMEP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CK(call, where)                          \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+lmep_status check_grid(const lmep_grid* g, int n_phi) {
+  if (!g) return fail(LMEP_ERR_INVALID, "grid is NULL");
+  if (g->n < 3 || g->n > 15 || (g->n % 2) == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15");
+  if (g->N < g->n) return fail(LMEP_ERR_INVALID, "N must be >= n");
+  if (g->N > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "N too large");
+  if (!(g->h > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
+  if (g->bc < 0 || g->bc > 2) return fail(LMEP_ERR_INVALID, "unknown boundary condition");
+  if (n_phi < 0 || n_phi > 2) return fail(LMEP_ERR_INVALID, "n_phi must be 0, 1 or 2");
+  if (g->n + n_phi > 16) return fail(LMEP_ERR_UNSUPPORTED, "n + n_phi must be <= 16");
+  return LMEP_OK;
+}
+
+lmep_status check_prec(int32_t precision) {
+  if (precision != LMEP_PREC_FP64 && precision != LMEP_PREC_MIXED)
+    return fail(LMEP_ERR_INVALID, "precision must be LMEP_PREC_FP64 or LMEP_PREC_MIXED");
+  return LMEP_OK;
+}
+
+KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int n_phi) {
+  KParams p{};
+  p.N = g->N;
+  p.h = g->h;
+  p.bc = g->bc;
+  p.n = g->n;
+  p.dep = g->departure_centring ? 1 : 0;
+  p.n_phi = n_phi;
+  p.bc_lo = g->bc_lo;
+  p.bc_hi = g->bc_hi;
+  p.dt = dt;
+  p.c0 = op->c0;
+  p.c1 = op->c1;
+  p.c2 = op->c2;
+  p.c3 = op->c3;
+  p.fa = op->frozen_adv;
+  return p;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int default_tile(bool mixed) { return mixed ? 2048 : 1024; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lmep_version(void) { return "lmep-gb300 0.1 (sm_103a)"; }
+
+const char* lmep_last_error(void) { return g_last_error.c_str(); }
+
+const char* lmep_status_string(lmep_status s) {
+  switch (s) {
+    case LMEP_OK: return "ok";
+    case LMEP_ERR_INVALID: return "invalid argument";
+    case LMEP_ERR_CUDA: return "CUDA error";
+    case LMEP_ERR_NONFINITE: return "non-finite result";
+    case LMEP_ERR_TIMEOUT: return "timeout";
+    case LMEP_ERR_UNSUPPORTED: return "unsupported shape";
+    case LMEP_ERR_NOMEM: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+lmep_status lmep_create(lmep_handle** out) {
+  if (!out) return fail(LMEP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  unsigned* flags = nullptr;
+  CK(cudaMalloc(&flags, 256), "cudaMalloc(status)");
+  cudaError_t e = cudaMemset(flags, 0, 256);
+  if (e != cudaSuccess) {
+    cudaFree(flags);
+    return cuda_fail(e, "cudaMemset(status)");
+  }
+  lmep_handle* h = new lmep_handle();
+  h->device = dev;
+  h->flags = flags;
+  *out = h;
+  return LMEP_OK;
+}
+
+lmep_status lmep_destroy(lmep_handle* h) {
+  if (!h) return LMEP_OK;
+  cudaFree(h->flags);
+  delete h;
+  return LMEP_OK;
+}
+
+lmep_status lmep_build_operator(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                                int32_t n_phi, const double* u_dev, int64_t i0, int64_t count,
+                                double* M_dev, int32_t* start_dev, int32_t* row_dev, void* stream) {
+  if (!h || !op) return fail(LMEP_ERR_INVALID, "handle/operator is NULL");
+  lmep_status st = check_grid(g, n_phi);
+  if (st != LMEP_OK) return st;
+  if (count < 0 || i0 < 0 || i0 + count > g->N) return fail(LMEP_ERR_INVALID, "point range outside grid");
+  if (count == 0) return LMEP_OK;
+  if (!M_dev || !start_dev || !row_dev) return fail(LMEP_ERR_INVALID, "output pointer is NULL");
+  if (op->frozen_adv != 0.0 && !u_dev) return fail(LMEP_ERR_INVALID, "frozen operator needs u_dev");
+  CK(lmep::launch_build_operator(make_params(g, op, dt, n_phi), u_dev, i0, count, M_dev, start_dev,
+                                 row_dev, S(stream)),
+     "build_operator");
+  return LMEP_OK;
+}
+
+lmep_status lmep_expm(lmep_handle* h, const double* A_dev, int64_t P, int32_t d, double* E_dev,
+                      int32_t precision, int32_t* ms_dev, void* stream) {
+  if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
+  if (d < 3 || d > 16) return fail(LMEP_ERR_UNSUPPORTED, "d must be 3..16");
+  if (P < 0) return fail(LMEP_ERR_INVALID, "P < 0");
+  lmep_status st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  if (P == 0) return LMEP_OK;
+  if (!A_dev || !E_dev) return fail(LMEP_ERR_INVALID, "NULL matrix pointer");
+  CK(lmep::launch_expm(A_dev, P, d, E_dev, precision == LMEP_PREC_MIXED, ms_dev, S(stream)), "expm");
+  return LMEP_OK;
+}
+
+lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                                 int32_t n_phi, const void* u_frozen_dev, void* W_dev, int32_t precision,
+                                 void* stream) {
+  if (!h || !op || !W_dev) return fail(LMEP_ERR_INVALID, "NULL handle/operator/W");
+  lmep_status st = check_grid(g, n_phi);
+  if (st != LMEP_OK) return st;
+  st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  const KParams p = make_params(g, op, dt, n_phi);
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  if (u_frozen_dev) {
+    if (n_phi != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity weights need n_phi == 0");
+    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen weights need N >= 2n");
+    CK(lmep::launch_frozen(p, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream)), "harvest(frozen)");
+    return LMEP_OK;
+  }
+  if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "frozen operator needs u_frozen_dev");
+  CK(lmep::launch_harvest_const(p, nullptr, 1, W_dev, mixed, S(stream)), "harvest(constant)");
+  return LMEP_OK;
+}
+
+lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, int32_t scheme,
+                      int32_t nonlin, double dt, const void* W_dev, void* u_dev, void* work_dev,
+                      int64_t nsteps, int32_t precision, void* stream) {
+  if (!h || !op) return fail(LMEP_ERR_INVALID, "NULL handle/operator");
+  if (scheme < 0 || scheme > 2) return fail(LMEP_ERR_INVALID, "unknown scheme");
+  if (nonlin < 0 || nonlin > 2) return fail(LMEP_ERR_INVALID, "unknown nonlinearity");
+  if ((scheme == 0) != (nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
+  lmep_status st = check_grid(g, scheme);
+  if (st != LMEP_OK) return st;
+  st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  if (nsteps < 0) return fail(LMEP_ERR_INVALID, "nsteps < 0");
+  if (!u_dev || !work_dev) return fail(LMEP_ERR_INVALID, "NULL state buffer");
+  if (u_dev == work_dev) return fail(LMEP_ERR_INVALID, "u_dev and work_dev must differ");
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  if (nsteps == 0) return LMEP_OK;
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  const size_t es = mixed ? 4 : 8;
+  void* cur = u_dev;
+  void* nxt = work_dev;
+  if (!W_dev) {
+    if (scheme != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity stepping uses the linear scheme");
+    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen step needs N >= 2n");
+    if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "W_dev is NULL but the operator is not frozen");
+    const KParams p = make_params(g, op, dt, 0);
+    for (int64_t t = 0; t < nsteps; ++t) {
+      CK(lmep::launch_frozen(p, cur, nxt, true, mixed, h->flags, S(stream)), "step(frozen)");
+      std::swap(cur, nxt);
+    }
+  } else {
+    if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
+    if (nonlin == 2 && g->bc != LMEP_BC_PERIODIC) return fail(LMEP_ERR_UNSUPPORTED, "KdV needs a periodic grid");
+    const int H = lmep::apply_halo(g->n, scheme, nonlin, g->bc);
+    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 2) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
+    ApplyParams a{};
+    a.halo = H;
+    a.n = g->n;
+    a.scheme = scheme;
+    a.nonlin = nonlin;
+    a.tile = default_tile(mixed);
+    if (g->bc == LMEP_BC_DIRICHLET && a.tile < 4 * g->n) a.tile = 4 * g->n;
+    a.dt = dt;
+    a.bc_lo = g->bc_lo;
+    a.bc_hi = g->bc_hi;
+    a.inst = nullptr;
+    a.tiles = nullptr;
+    a.ntiles = (g->N + a.tile - 1) / a.tile;
+    a.wq = 1 + scheme;
+    a.w_stride = int64_t(g->n) * a.wq * g->n;
+    a.N = g->N;
+    a.h = g->h;
+    a.bc = g->bc;
+    const int block = 256;
+    const int grid = lmep::apply_grid(a, block, 0, mixed);
+    for (int64_t t = 0; t < nsteps; ++t) {
+      CK(lmep::launch_apply(a, cur, nxt, W_dev, mixed, block, grid, h->flags, S(stream)), "step(apply)");
+      std::swap(cur, nxt);
+    }
+  }
+  if (cur != u_dev) CK(cudaMemcpyAsync(u_dev, cur, size_t(g->N) * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
+  return LMEP_OK;
+}
+
+// ------------------------------------------------------------------ batches
+namespace {
+struct BatchLayout {
+  size_t inst_off, tiles_off, h_off, w_off, total;
+  int64_t ntiles;
+  int tile;
+};
+lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayout* L) {
+  if (!d || d->B <= 0 || !d->N_host || !d->h_host || !d->bc_host) return fail(LMEP_ERR_INVALID, "bad batch descriptor");
+  if (d->n < 3 || d->n > 15 || d->n % 2 == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15");
+  if (d->scheme < 0 || d->scheme > 2 || d->n + d->scheme > 16) return fail(LMEP_ERR_INVALID, "bad scheme");
+  if (d->nonlin == 2) return fail(LMEP_ERR_UNSUPPORTED, "KdV batches are not supported");
+  if ((d->scheme == 0) != (d->nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
+  if (d->op.frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "batches use constant operators");
+  lmep_status st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  int tile = d->tile > 0 ? d->tile : default_tile(mixed);
+  if (tile % 256 != 0 || tile > 16384) return fail(LMEP_ERR_INVALID, "tile must be a multiple of 256, <= 16384");
+  if (d->block != 0 && d->block != 128 && d->block != 256 && d->block != 512)
+    return fail(LMEP_ERR_INVALID, "block must be 128, 256 or 512");
+  const int H = lmep::apply_halo(d->n, d->scheme, d->nonlin, LMEP_BC_PERIODIC);
+  int64_t ntiles = 0;
+  for (int64_t b = 0; b < d->B; ++b) {
+    const int64_t N = d->N_host[b];
+    if (d->bc_host[b] != LMEP_BC_PERIODIC && d->bc_host[b] != LMEP_BC_NEUMANN)
+      return fail(LMEP_ERR_INVALID, "batch instances must be periodic or Neumann");
+    if (N < 2 * H + 2 || N < d->n) return fail(LMEP_ERR_UNSUPPORTED, "instance too small for the halo");
+    if (!(d->h_host[b] > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
+    ntiles += (N + tile - 1) / tile;
+  }
+  if (ntiles > (int64_t(1) << 31) - 1) return fail(LMEP_ERR_INVALID, "too many tiles");
+  const size_t es = mixed ? 4 : 8;
+  L->tile = tile;
+  L->ntiles = ntiles;
+  L->inst_off = 256;
+  L->tiles_off = align_up(L->inst_off + size_t(d->B) * sizeof(Instance), 256);
+  L->h_off = align_up(L->tiles_off + size_t(ntiles) * sizeof(int2), 256);
+  L->w_off = align_up(L->h_off + size_t(d->B) * sizeof(double), 256);
+  L->total = align_up(L->w_off + size_t(d->B) * d->n * (1 + d->scheme) * d->n * es, 256);
+  return LMEP_OK;
+}
+}  // namespace
+
+lmep_status lmep_batch_workspace_bytes(const lmep_batch_desc* d, int32_t precision, size_t* bytes_out) {
+  if (!bytes_out) return fail(LMEP_ERR_INVALID, "bytes_out is NULL");
+  BatchLayout L;
+  lmep_status st = batch_layout(d, precision, &L);
+  if (st != LMEP_OK) return st;
+  *bytes_out = L.total;
+  return LMEP_OK;
+}
+
+lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* ws, size_t bytes,
+                               int32_t precision, void* stream) {
+  if (!h || !ws) return fail(LMEP_ERR_INVALID, "NULL handle/workspace");
+  if (!aligned16(ws)) return fail(LMEP_ERR_INVALID, "workspace must be 16-byte aligned");
+  BatchLayout L;
+  lmep_status st = batch_layout(d, precision, &L);
+  if (st != LMEP_OK) return st;
+  if (bytes < L.total) return fail(LMEP_ERR_NOMEM, "workspace smaller than lmep_batch_workspace_bytes");
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  std::vector<Instance> inst(size_t(d->B));
+  std::vector<int2> tiles;
+  tiles.reserve(size_t(L.ntiles));
+  int64_t off = 0;
+  for (int64_t b = 0; b < d->B; ++b) {
+    inst[b].off = off;
+    inst[b].N = d->N_host[b];
+    inst[b].h = d->h_host[b];
+    inst[b].bc = d->bc_host[b];
+    inst[b].pad = 0;
+    for (int64_t t0 = 0; t0 < inst[b].N; t0 += L.tile) tiles.push_back(make_int2(int(b), int(t0)));
+    off += inst[b].N;
+  }
+  char* base = static_cast<char*>(ws);
+  CK(cudaMemcpyAsync(base + L.inst_off, inst.data(), inst.size() * sizeof(Instance), cudaMemcpyHostToDevice,
+                     S(stream)), "copy(instances)");
+  CK(cudaMemcpyAsync(base + L.tiles_off, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                     S(stream)), "copy(tiles)");
+  CK(cudaMemcpyAsync(base + L.h_off, d->h_host, size_t(d->B) * sizeof(double), cudaMemcpyHostToDevice,
+                     S(stream)), "copy(h)");
+  // weights of every instance, harvested on the device
+  lmep_grid g{};
+  g.N = 1 << 20;
+  g.h = 1.0;
+  g.bc = LMEP_BC_PERIODIC;
+  g.n = d->n;
+  KParams p = make_params(&g, &d->op, d->dt, d->scheme);
+  CK(lmep::launch_harvest_const(p, reinterpret_cast<const double*>(base + L.h_off), d->B, base + L.w_off,
+                                mixed, S(stream)), "harvest(batch)");
+  // the host copies above read pageable vectors: make sure they are consumed
+  CK(cudaStreamSynchronize(S(stream)), "sync(prepare)");
+  BatchPlan plan{};
+  ApplyParams& a = plan.ap;
+  a.n = d->n;
+  a.scheme = d->scheme;
+  a.nonlin = d->nonlin;
+  a.halo = lmep::apply_halo(d->n, d->scheme, d->nonlin, LMEP_BC_PERIODIC);
+  a.tile = L.tile;
+  a.dt = d->dt;
+  a.inst = reinterpret_cast<const Instance*>(base + L.inst_off);
+  a.tiles = reinterpret_cast<const int2*>(base + L.tiles_off);
+  a.ntiles = L.ntiles;
+  a.wq = 1 + d->scheme;
+  a.w_stride = int64_t(d->n) * a.wq * d->n;
+  a.N = 0;
+  a.h = 1.0;
+  a.bc = LMEP_BC_PERIODIC;
+  plan.W = base + L.w_off;
+  plan.points = off;
+  plan.block = d->block > 0 ? d->block : 256;
+  plan.mixed = mixed;
+  plan.grid = lmep::apply_grid(a, plan.block, d->ctas_per_sm, mixed);
+  plan.bytes = L.total;
+  h->plans[ws] = plan;
+  return LMEP_OK;
+}
+
+lmep_status lmep_step_batched(lmep_handle* h, const void* ws, void* u_dev, void* work_dev, int64_t nsteps,
+                              void* stream) {
+  if (!h || !ws || !u_dev || !work_dev) return fail(LMEP_ERR_INVALID, "NULL argument");
+  if (u_dev == work_dev) return fail(LMEP_ERR_INVALID, "u_dev and work_dev must differ");
+  auto it = h->plans.find(ws);
+  if (it == h->plans.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
+  if (nsteps < 0) return fail(LMEP_ERR_INVALID, "nsteps < 0");
+  const BatchPlan& plan = it->second;
+  void* cur = u_dev;
+  void* nxt = work_dev;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    CK(lmep::launch_apply(plan.ap, cur, nxt, plan.W, plan.mixed, plan.block, plan.grid, h->flags, S(stream)),
+       "step_batched");
+    std::swap(cur, nxt);
+  }
+  const size_t es = plan.mixed ? 4 : 8;
+  if (cur != u_dev)
+    CK(cudaMemcpyAsync(u_dev, cur, size_t(plan.points) * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
+  return LMEP_OK;
+}
+
+lmep_status lmep_adjoint_scratch_bytes(const lmep_grid* g, int32_t precision, size_t* bytes_out) {
+  if (!bytes_out) return fail(LMEP_ERR_INVALID, "bytes_out is NULL");
+  lmep_status st = check_grid(g, 0);
+  if (st != LMEP_OK) return st;
+  st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  *bytes_out = lmep::adjoint_scratch_bytes(g->N, g->n, precision == LMEP_PREC_MIXED);
+  return LMEP_OK;
+}
+
+lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                              const void* u_dev, const void* lam_next_dev, void* lam_dev, double* dnu_dev,
+                              void* scratch_dev, size_t scratch_bytes, int32_t precision, void* stream) {
+  if (!h || !op) return fail(LMEP_ERR_INVALID, "NULL handle/operator");
+  lmep_status st = check_grid(g, 0);
+  if (st != LMEP_OK) return st;
+  st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  if (g->bc == LMEP_BC_NEUMANN) return fail(LMEP_ERR_UNSUPPORTED, "adjoint supports periodic and Dirichlet grids");
+  if (g->bc == LMEP_BC_PERIODIC && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "periodic adjoint needs N >= 2n");
+  if (!u_dev || !lam_next_dev || !lam_dev || !dnu_dev || !scratch_dev) return fail(LMEP_ERR_INVALID, "NULL buffer");
+  if (lam_dev == lam_next_dev) return fail(LMEP_ERR_INVALID, "lam_dev must differ from lam_next_dev");
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  if (scratch_bytes < lmep::adjoint_scratch_bytes(g->N, g->n, mixed)) return fail(LMEP_ERR_NOMEM, "scratch too small");
+  CK(lmep::launch_adjoint(make_params(g, op, dt, 0), u_dev, lam_next_dev, lam_dev, dnu_dev, scratch_dev, mixed,
+                          h->flags, S(stream)), "adjoint");
+  return LMEP_OK;
+}
+
+lmep_status lmep_sync_status(lmep_handle* h, void* stream) {
+  if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
+  CK(cudaStreamSynchronize(S(stream)), "cudaStreamSynchronize");
+  unsigned flags = 0;
+  CK(cudaMemcpy(&flags, h->flags, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
+  if (flags) {
+    CK(cudaMemset(h->flags, 0, sizeof(unsigned)), "clear status");
+    return fail(LMEP_ERR_NONFINITE, "a kernel produced a non-finite value");
+  }
+  return LMEP_OK;
+}
+
+lmep_status lmep_fma_peak(int32_t precision, double* flops_out) {
+  if (!flops_out) return fail(LMEP_ERR_INVALID, "flops_out is NULL");
+  lmep_status st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  CK(lmep::fma_peak(precision == LMEP_PREC_MIXED, flops_out), "fma_peak");
+  return LMEP_OK;
+}
+
+}  // extern "C"

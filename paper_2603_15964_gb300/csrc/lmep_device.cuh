@@ -1,0 +1,514 @@
+// lmep_device.cuh -- device building blocks of the LMEP hot path (sm_103a).
+//
+// One warp owns one small matrix (dimension d <= 16) in shared memory:
+//   * Fornberg derivative weights on the integer window nodes (Sec. 2.1 step 1),
+//   * stencil window / harvest row selection (Sec. 2.1 steps 1 and 3),
+//   * Pade [m/m] scaling and squaring exp(X) (Sec. 2.1 step 2; Higham 2005,
+//     "The scaling and squaring method for the matrix exponential revisited",
+//     Algorithm 2.3, degree choice by ||X||_1 against theta_m of its Table 2.3),
+//     with the polynomial products in PT (double, or float for the FP32 form),
+//     the denominator solve by Gauss-Jordan elimination with partial pivoting
+//     in FP64, and the squaring phase in FP64.  Because only a few rows of
+//     exp(X) are harvested, the last 2^b factors of the squaring phase are
+//     applied to those rows only (row vector times R, repeated).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lmep {
+
+constexpr int DMAX = 16;        // largest matrix handled by one warp
+constexpr int LD = 17;          // leading dimension of a d x d matrix in shared memory
+constexpr int LDG = 2 * DMAX + 1;  // leading dimension of the d x 2d Gauss-Jordan block
+constexpr unsigned FULL = 0xffffffffu;
+
+// Backward-error bounds theta_m of Higham (2005), Table 2.3.
+constexpr double THETA3 = 1.495585217958292e-2;
+constexpr double THETA5 = 2.539398330063230e-1;
+constexpr double THETA7 = 9.504178996162932e-1;
+constexpr double THETA9 = 2.097847961257068e0;
+constexpr double THETA13 = 5.371920351148152e0;
+
+// Coefficient of x^j in the numerator of the [m/m] Pade approximant of e^x,
+// normalised to b_0 = 1: b_{j+1} = b_j (m - j) / ((2m - j)(j + 1)).
+__host__ __device__ constexpr double pade_b(int m, int j) {
+  double b = 1.0;
+  for (int t = 0; t < j; ++t) b = b * double(m - t) / (double(2 * m - t) * double(t + 1));
+  return b;
+}
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- Fornberg (a2)
+// Weights c[k][j] of d^k/dx^k (k = 0..3) at z from the integer nodes 0..n-1,
+// built by adding one node at a time (Fornberg 1988 recursion, in-place form
+// with descending derivative order).  Per thread; used once per CTA.
+__device__ inline void fornberg_row(double z, int n, double c[4][DMAX]) {
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < DMAX; ++j) c[k][j] = 0.0;
+  c[0][0] = 1.0;
+  double c1 = 1.0, c4 = -z;
+  for (int i = 1; i < n; ++i) {
+    const int mn = i < 3 ? i : 3;
+    double c2 = 1.0;
+    const double c5 = c4;
+    c4 = double(i) - z;
+    for (int j = 0; j < i; ++j) {
+      const double c3 = double(i - j);
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int k = mn; k >= 1; --k) c[k][i] = c1 * (k * c[k - 1][i - 1] - c5 * c[k][i - 1]) / c2;
+        c[0][i] = -c1 * c5 * c[0][i - 1] / c2;
+      }
+      for (int k = mn; k >= 1; --k) c[k][j] = (c4 * c[k][j] - k * c[k - 1][j]) / c3;
+      c[0][j] = c4 * c[0][j] / c3;
+    }
+    c1 = c2;
+  }
+}
+
+// Fill Dh[k-1][i*LD + j] = h^k D^(k)[i][j] (k = 1..3) for the uniform window of
+// width n in shared memory.  Threads 0..n-1 of the block each build one row.
+// Caller synchronises.
+__device__ inline void fornberg_block(double* Dh, int n) {
+  const int t = threadIdx.x;
+  if (t < n) {
+    double c[4][DMAX];
+    fornberg_row(double(t), n, c);
+    for (int k = 1; k <= 3; ++k)
+      for (int j = 0; j < n; ++j) Dh[(k - 1) * DMAX * LD + t * LD + j] = c[k][j];
+  }
+}
+
+// ---------------------------------------------------------------- stencils (a1)
+enum { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_NEUMANN = 2 };
+
+// Window start of point i (global index of window node 0 before wrap or
+// reflection) with an upstream shift k; the harvest row is i - start.
+__device__ __forceinline__ int64_t window_start(int64_t i, int64_t N, int n, int bc, int k) {
+  const int hs = (n - 1) >> 1;
+  int64_t s = i - hs - k;
+  if (bc == BC_DIRICHLET) s = s < 0 ? 0 : (s > N - n ? N - n : s);
+  return s;
+}
+// Map a possibly out-of-range index to the grid (periodic wrap, even reflection).
+__device__ __forceinline__ int64_t grid_index(int64_t q, int64_t N, int bc) {
+  if (bc == BC_PERIODIC) {
+    q %= N;
+    return q < 0 ? q + N : q;
+  }
+  if (bc == BC_NEUMANN) {
+    if (q < 0) q = -q;
+    if (q > N - 1) q = 2 * (N - 1) - q;
+    return q;
+  }
+  return q;
+}
+// Departure-centring shift clamp(floor(u dt / h + 1/2), -hs, hs), evaluated
+// with explicitly rounded FP64 operations so that the integer decision is
+// reproducible bit for bit.
+__device__ __forceinline__ int departure_shift(double u, double dt, double h, int n) {
+  const int hs = (n - 1) >> 1;
+  const double t = __dadd_rn(__ddiv_rn(__dmul_rn(u, dt), h), 0.5);
+  // fmin/fmax return the non-NaN operand, so a non-finite state still gives a
+  // window inside the clamp range (the non-finite result is flagged later).
+  const double k = fmax(double(-hs), fmin(double(hs), floor(t)));
+  return int(k);
+}
+// Exact integer re-centring of an exponential row: row r of exp(X(a)) equals
+// row r - k of exp(X(a) + k Dh1) (both evaluate e^{dt L} p at the same
+// departure point, Thm. 2).  k is the rounded local Courant number
+// -dt a1 / h, kept so that row r - k exists.
+__device__ __forceinline__ int recentring_shift(double a1, double dt, double h, int n, int r) {
+  const double cfl = __ddiv_rn(__dmul_rn(-dt, a1), h);
+  const double k = fmax(double(r - (n - 1)), fmin(double(r), floor(__dadd_rn(cfl, 0.5))));
+  return int(k);
+}
+
+// ---------------------------------------------------------------- warp expm (a4)
+// Per-warp shared workspace layout (bytes):
+//   X64  double d x d (LD)         the (scaled-before-conversion) input
+//   PRD  5 x PT d x d (LD)         X, X^2, X^4, X^6 (or X^8), temporary
+//   G    double d x 2d (LDG)       [Q | P] -> [. | Q^-1 P]
+//   R1   double d x d (LD)         squaring ping-pong
+//   R2   double d x d (LD)         squaring ping-pong
+//   VEC  double 4 x 16             harvested rows
+template <typename PT>
+struct Ws {
+  static constexpr int X64_OFF = 0;
+  static constexpr int PRD_OFF = X64_OFF + DMAX * LD * 8;
+  static constexpr int G_OFF = PRD_OFF + 5 * DMAX * LD * int(sizeof(PT));
+  static constexpr int R1_OFF = G_OFF + DMAX * LDG * 8;
+  static constexpr int R2_OFF = R1_OFF + DMAX * LD * 8;
+  static constexpr int VEC_OFF = R2_OFF + DMAX * LD * 8;
+  static constexpr int BYTES = VEC_OFF + 4 * DMAX * 8;
+  double* X64;
+  PT* P;  // 5 product matrices back to back
+  double* G;
+  double* R1;
+  double* R2;
+  double* V;
+  __device__ explicit Ws(unsigned char* base)
+      : X64(reinterpret_cast<double*>(base + X64_OFF)),
+        P(reinterpret_cast<PT*>(base + PRD_OFF)),
+        G(reinterpret_cast<double*>(base + G_OFF)),
+        R1(reinterpret_cast<double*>(base + R1_OFF)),
+        R2(reinterpret_cast<double*>(base + R2_OFF)),
+        V(reinterpret_cast<double*>(base + VEC_OFF)) {}
+  __device__ PT* M(int q) const { return P + q * DMAX * LD; }
+};
+
+// Element slots of a d x d matrix spread over a warp: lane owns e = lane + 32 t.
+template <int D>
+struct Slots {
+  static constexpr int S = (D * D + 31) / 32;
+  int i[S], j[S];
+  bool ok[S];
+  __device__ explicit Slots(int lane) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int e = lane + 32 * t;
+      ok[t] = e < D * D;
+      i[t] = ok[t] ? e / D : 0;
+      j[t] = ok[t] ? e - (e / D) * D : 0;
+    }
+  }
+};
+
+// acc = A B for the lane's slots (A stride LDA, B stride LDB).
+template <int D, int LDA, int LDB, typename T>
+__device__ __forceinline__ void mm_slots(const T* __restrict__ A, const T* __restrict__ B,
+                                         T (&acc)[Slots<D>::S], const Slots<D>& sl) {
+  constexpr int S = Slots<D>::S;
+#pragma unroll
+  for (int t = 0; t < S; ++t) acc[t] = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) acc[t] = fma(A[sl.i[t] * LDA + k], B[k * LDB + sl.j[t]], acc[t]);
+  }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void store_slots(T* __restrict__ C, const T (&v)[Slots<D>::S],
+                                            const Slots<D>& sl) {
+#pragma unroll
+  for (int t = 0; t < Slots<D>::S; ++t)
+    if (sl.ok[t]) C[sl.i[t] * LD + sl.j[t]] = v[t];
+}
+
+// v = c0*M0 + c1*M1 + c2*M2 (+ cI on the diagonal), per slot, read from shared memory.
+template <int D, typename T>
+__device__ __forceinline__ void lincomb(T (&v)[Slots<D>::S], const Slots<D>& sl, const T* M0, T c0,
+                                        const T* M1, T c1, const T* M2, T c2, T cI, bool add) {
+#pragma unroll
+  for (int t = 0; t < Slots<D>::S; ++t) {
+    const int o = sl.i[t] * LD + sl.j[t];
+    T x = add ? v[t] : T(0);
+    if (M0) x = fma(c0, M0[o], x);
+    if (M1) x = fma(c1, M1[o], x);
+    if (M2) x = fma(c2, M2[o], x);
+    if (sl.i[t] == sl.j[t]) x += cI;
+    v[t] = x;
+  }
+}
+
+// Pade degree m and squarings s from ||X||_1 (Higham 2005, Algorithm 2.3).
+__device__ __forceinline__ void choose_ms(double nrm, int& m, int& s) {
+  s = 0;
+  if (nrm <= THETA3) m = 3;
+  else if (nrm <= THETA5) m = 5;
+  else if (nrm <= THETA7) m = 7;
+  else if (nrm <= THETA9) m = 9;
+  else {
+    m = 13;
+    // smallest s >= 0 with nrm / 2^s <= theta_13 (exact power-of-two test)
+    double t = nrm;
+    while (t > THETA13 && s < 1023) { t *= 0.5; ++s; }
+  }
+}
+
+// Odd part U and even part V of p_m(X) for the lane's slots; X is PRD slot 0.
+// Products follow Higham (2005) eqs. (2.10)-(2.11); the degree only changes
+// which powers exist and which coefficients multiply them, so every degree
+// shares the same product call sites.  Uses PRD slots 1..4.
+template <int D, typename PT>
+__device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& sl, PT (&U)[Slots<D>::S],
+                                        PT (&V)[Slots<D>::S]) {
+  constexpr int S = Slots<D>::S;
+  PT* X = w.M(0);
+  PT* A2 = w.M(1);
+  PT* A4 = w.M(2);
+  PT* A6 = w.M(3);
+  PT* T = w.M(4);
+  PT acc[S], A8[S];
+  PT b[14];
+#pragma unroll
+  for (int j = 0; j < 14; ++j) b[j] = PT(0);
+  switch (m) {
+    case 3:
+#pragma unroll
+      for (int j = 0; j <= 3; ++j) b[j] = PT(pade_b(3, j));
+      break;
+    case 5:
+#pragma unroll
+      for (int j = 0; j <= 5; ++j) b[j] = PT(pade_b(5, j));
+      break;
+    case 7:
+#pragma unroll
+      for (int j = 0; j <= 7; ++j) b[j] = PT(pade_b(7, j));
+      break;
+    case 9:
+#pragma unroll
+      for (int j = 0; j <= 9; ++j) b[j] = PT(pade_b(9, j));
+      break;
+    default:
+#pragma unroll
+      for (int j = 0; j <= 13; ++j) b[j] = PT(pade_b(13, j));
+  }
+  // powers X^2, X^4, X^6 (and X^8 in registers for m = 9)
+  mm_slots<D, LD, LD>(X, X, acc, sl);
+  store_slots<D>(A2, acc, sl);
+  __syncwarp();
+  if (m >= 5) {
+    mm_slots<D, LD, LD>(A2, A2, acc, sl);
+    store_slots<D>(A4, acc, sl);
+    __syncwarp();
+  }
+  if (m >= 7) {
+    mm_slots<D, LD, LD>(A4, A2, acc, sl);
+    store_slots<D>(A6, acc, sl);
+    __syncwarp();
+  }
+  if (m == 9) mm_slots<D, LD, LD>(A6, A2, A8, sl);
+  const PT* P2 = A2;
+  const PT* P4 = m >= 5 ? A4 : nullptr;
+  const PT* P6 = m >= 7 ? A6 : nullptr;
+  if (m == 13) {
+    // U-inner = A6 (b13 A6 + b11 A4 + b9 A2) + b7 A6 + b5 A4 + b3 A2 + b1 I
+    // V       = A6 (b12 A6 + b10 A4 + b8 A2) + b6 A6 + b4 A4 + b2 A2 + b0 I
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      const int o = pass == 0 ? 1 : 0;  // odd (U-inner) or even (V) coefficients
+      lincomb<D>(acc, sl, A6, b[12 + o], A4, b[10 + o], A2, b[8 + o], PT(0), false);
+      __syncwarp();
+      store_slots<D>(T, acc, sl);
+      __syncwarp();
+      mm_slots<D, LD, LD>(A6, T, acc, sl);
+      lincomb<D>(acc, sl, A6, b[6 + o], A4, b[4 + o], A2, b[2 + o], b[o], true);
+      if (pass == 0) {
+#pragma unroll
+        for (int t = 0; t < S; ++t) U[t] = acc[t];
+      } else {
+#pragma unroll
+        for (int t = 0; t < S; ++t) V[t] = acc[t];
+      }
+    }
+    // U-inner goes back to T for the final product
+    __syncwarp();
+    store_slots<D>(T, U, sl);
+  } else {
+    lincomb<D>(acc, sl, P6, b[7], P4, b[5], P2, b[3], b[1], false);
+    lincomb<D>(V, sl, P6, b[6], P4, b[4], P2, b[2], b[0], false);
+    if (m == 9) {
+#pragma unroll
+      for (int t = 0; t < S; ++t) {
+        acc[t] = fma(b[9], A8[t], acc[t]);
+        V[t] = fma(b[8], A8[t], V[t]);
+      }
+    }
+    store_slots<D>(T, acc, sl);
+  }
+  __syncwarp();
+  mm_slots<D, LD, LD>(X, T, U, sl);
+  __syncwarp();
+}
+
+// Solve Q R = P in place on G = [Q | P] by Gauss-Jordan elimination with
+// partial pivoting (FP64).  On return G[:, D:2D] holds R.  Pivot magnitudes
+// are compared as IEEE bit patterns (monotonic for non-negative doubles).
+template <int D>
+__device__ void gauss_jordan(double* G, int lane) {
+  for (int k = 0; k < D; ++k) {
+    long long key = -1;
+    int idx = k;
+    if (lane >= k && lane < D) {
+      key = __double_as_longlong(G[lane * LDG + k]) & 0x7fffffffffffffffll;
+      idx = lane;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const long long ok = __shfl_xor_sync(FULL, key, o);
+      const int oi = __shfl_xor_sync(FULL, idx, o);
+      if (ok > key || (ok == key && oi < idx)) {
+        key = ok;
+        idx = oi;
+      }
+    }
+    if (idx != k) {
+      for (int j = k + lane; j < 2 * D; j += 32) {
+        const double a = G[k * LDG + j];
+        G[k * LDG + j] = G[idx * LDG + j];
+        G[idx * LDG + j] = a;
+      }
+    }
+    __syncwarp();
+    const double inv = __drcp_rn(G[k * LDG + k]);
+    for (int j = k + 1 + lane; j < 2 * D; j += 32) G[k * LDG + j] *= inv;
+    __syncwarp();
+    const int nc = 2 * D - k - 1;
+    const int tot = (D - 1) * nc;
+    const float rnc = 1.0f / float(nc);
+    for (int e = lane; e < tot; e += 32) {
+      const int ii = __float2int_rz((float(e) + 0.5f) * rnc);
+      const int jj = e - ii * nc;
+      const int i = ii + (ii >= k ? 1 : 0);
+      const int j = k + 1 + jj;
+      G[i * LDG + j] = fma(-G[i * LDG + k], G[k * LDG + j], G[i * LDG + j]);
+    }
+    __syncwarp();
+  }
+}
+
+// Row-vector phase: V[q][:] <- V[q][:] * R, nrows rows, FP64.  R has stride ldr.
+template <int D>
+__device__ __forceinline__ void rows_times(double* V, const double* R, int ldr, int nrows, int lane) {
+  if (nrows == 1) {
+    // split the k-sum over the two half-warps, then combine with one shuffle
+    constexpr int K0 = (D + 1) / 2;
+    const int j = lane & 15, half = lane >> 4;
+    double acc = 0.0;
+    if (j < D) {
+      if (half == 0) {
+#pragma unroll
+        for (int k = 0; k < K0; ++k) acc = fma(V[k], R[k * ldr + j], acc);
+      } else {
+#pragma unroll
+        for (int k = K0; k < D; ++k) acc = fma(V[k], R[k * ldr + j], acc);
+      }
+    }
+    acc += __shfl_xor_sync(FULL, acc, 16);
+    __syncwarp();
+    if (half == 0 && j < D) V[j] = acc;
+    __syncwarp();
+    return;
+  }
+  double res[2] = {0.0, 0.0};
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int o = lane + 32 * p;
+    if (o < nrows * D) {
+      const int q = o / D, j = o - (o / D) * D;
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = fma(V[q * DMAX + k], R[k * ldr + j], acc);
+      res[p] = acc;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int o = lane + 32 * p;
+    if (o < nrows * D) V[(o / D) * DMAX + (o - (o / D) * D)] = res[p];
+  }
+  __syncwarp();
+}
+
+// exp(X) for X = w.X64 (D x D, double).  Writes the harvested rows
+// rows[0..nrows) into w.V[q*DMAX + j] (double) when full == false, or the
+// whole exponential into E (stride lde) when full == true.  ms receives (m, s).
+template <int D, typename PT>
+__device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
+                          double* E, int lde, int* m_out, int* s_out) {
+  constexpr int S = Slots<D>::S;
+  const Slots<D> sl(lane);
+  // ||X||_1 = max column sum
+  double cs = 0.0;
+  if (lane < D) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) cs += fabs(w.X64[i * LD + lane]);
+  }
+  const double nrm = warp_max(cs);
+  int m, s;
+  choose_ms(nrm, m, s);
+  const double sc = ldexp(1.0, -s);
+  PT* X = w.M(0);
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (sl.ok[t]) X[sl.i[t] * LD + sl.j[t]] = PT(w.X64[sl.i[t] * LD + sl.j[t]] * sc);
+  __syncwarp();
+  PT U[S], V[S];
+  pade_uv<D, PT>(w, m, sl, U, V);
+  // [Q | P] = [V - U | V + U] in FP64
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    if (sl.ok[t]) {
+      const double u = double(U[t]), v = double(V[t]);
+      w.G[sl.i[t] * LDG + sl.j[t]] = v - u;
+      w.G[sl.i[t] * LDG + D + sl.j[t]] = v + u;
+    }
+  }
+  __syncwarp();
+  gauss_jordan<D>(w.G, lane);
+  // squaring phase in FP64: R = G[:, D:2D] copied to R1, full squarings
+  // ping-pong between R1 and R2, then the remaining 2^b factors are applied
+  // to the harvested rows only.
+#pragma unroll
+  for (int t = 0; t < S; ++t)
+    if (sl.ok[t]) w.R1[sl.i[t] * LD + sl.j[t]] = w.G[sl.i[t] * LDG + D + sl.j[t]];
+  __syncwarp();
+  int a = s;
+  if (!full) {
+    // a full squarings + 2^(s-a) - 1 row products, minimising FP64 instructions
+    const int cost_full = S * D;
+    const int cost_vec = nrows == 1 ? (D + 1) / 2 + 1 : D * ((nrows * D + 31) / 32);
+    // at most 2^6 - 1 row products; larger s always squares in full
+    int best = 1 << 30;
+    for (int aa = (s > 6 ? s - 6 : 0); aa <= s; ++aa) {
+      const int c = aa * cost_full + ((1 << (s - aa)) - 1) * cost_vec;
+      if (c < best) { best = c; a = aa; }
+    }
+  }
+  double* R = w.R1;
+  double* Rn = w.R2;
+  for (int q = 0; q < a; ++q) {
+    double acc[S];
+    mm_slots<D, LD, LD>(R, R, acc, sl);
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (sl.ok[t]) Rn[sl.i[t] * LD + sl.j[t]] = acc[t];
+    __syncwarp();
+    double* tmp = R;
+    R = Rn;
+    Rn = tmp;
+  }
+  if (full) {
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (sl.ok[t]) E[sl.i[t] * lde + sl.j[t]] = R[sl.i[t] * LD + sl.j[t]];
+  } else {
+    for (int o = lane; o < nrows * D; o += 32) {
+      const int q = o / D, j = o - (o / D) * D;
+      w.V[q * DMAX + j] = R[rows[q] * LD + j];
+    }
+    __syncwarp();
+    for (int q = 0; q < (1 << (s - a)) - 1; ++q) rows_times<D>(w.V, R, LD, nrows, lane);
+  }
+  __syncwarp();
+  if (m_out) *m_out = m;
+  if (s_out) *s_out = s;
+}
+
+}  // namespace lmep

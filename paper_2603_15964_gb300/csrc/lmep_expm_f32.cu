@@ -1,0 +1,8 @@
+// lmep_expm_f32.cu -- FP32-form instantiation of the warp kernel: Pade
+// products in FP32 with FP32 accumulation, denominator solve and squaring
+// phase in FP64, state and weights stored as float.
+#include "lmep_warp_kernel.cuh"
+
+namespace lmep {
+cudaError_t warp_job_f32(int d, const WarpJob& job, cudaStream_t s) { return dispatch_warp<float>(d, job, s); }
+}  // namespace lmep

@@ -1,0 +1,77 @@
+// lmep_internal.h -- launcher interface between the C ABI layer and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lmep {
+
+// Problem parameters passed by value to every kernel.
+struct KParams {
+  int64_t N;
+  double h;
+  int bc;
+  int n;
+  int dep;      // departure centring on/off
+  int n_phi;
+  double bc_lo, bc_hi;
+  double dt, c0, c1, c2, c3, fa;
+};
+
+struct DeviceInfo {
+  int sms;
+};
+DeviceInfo device_info();
+
+// ---- expm family (lmep_expm.cu)
+cudaError_t launch_build_operator(const KParams& p, const double* u, int64_t i0, int64_t count,
+                                  double* M, int32_t* start, int32_t* row, cudaStream_t s);
+cudaError_t launch_expm(const double* A, int64_t P, int d, double* E, bool mixed, int32_t* ms,
+                        cudaStream_t s);
+// Constant-coefficient weights for B instances (h_inst nullable -> p.h), W[b][n][1+n_phi][n].
+cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t B, void* W,
+                                 bool mixed, cudaStream_t s);
+// Frozen velocity: fused == false writes W[N][n]; fused == true writes u_out.
+cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
+                          unsigned* flags, cudaStream_t s);
+
+// ---- banded apply (lmep_apply.cu)
+struct Instance {
+  int64_t off;   // first element of the instance in the concatenated state
+  int64_t N;
+  double h;
+  int bc;
+  int pad;
+};
+struct ApplyParams {
+  int n, scheme, nonlin, tile;
+  int halo;          // staged halo per side (apply_halo)
+  double dt;
+  double bc_lo, bc_hi;
+  // instance table (device) and tile table (device, int2 = {instance, start})
+  const Instance* inst;
+  const int2* tiles;
+  int64_t ntiles;
+  int64_t w_stride;  // elements between the weight blocks of consecutive instances
+  int wq;            // weight rows stored per row class (1 + n_phi)
+  // single-instance fallback when inst == nullptr
+  int64_t N;
+  double h;
+  int bc;
+};
+int apply_halo(int n, int scheme, int nonlin, int bc);
+size_t apply_smem_bytes(int tile, int halo, int scheme, bool mixed);
+cudaError_t launch_apply(const ApplyParams& a, const void* u, void* out, const void* W, bool mixed,
+                         int block, int grid, unsigned* flags, cudaStream_t s);
+int apply_grid(const ApplyParams& a, int block, int ctas_per_sm, bool mixed);
+
+// ---- adjoint (lmep_adjoint.cu)
+size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed);
+cudaError_t launch_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam,
+                           double* dnu, void* scratch, bool mixed, unsigned* flags, cudaStream_t s);
+
+// ---- peak (lmep_peak.cu)
+cudaError_t fma_peak(bool fp32, double* flops);
+
+}  // namespace lmep
