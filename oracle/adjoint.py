@@ -16,7 +16,11 @@ matrix exponential in the directions E = dX_i/du_i = -dt D1 and
 E = dX_i/dnu = dt D2.  L(X, E) is the top-right block of
 exp([[X, E], [0, X]]) (Mathias 1996; Higham, "Functions of Matrices", 2008,
 Thm. 3.6).  The window shift of departure centring is piecewise constant in
-u_i and contributes nothing.  Test infrastructure only.
+u_i and contributes nothing.  Like the weights (``oracle.lmep.exp_row``), the
+Frechet rows are evaluated on the re-centred matrix X + k D-hat1: row r of
+exp(X(u)) equals row r - k of exp(X(u) + k D-hat1) for every u, so the same
+holds for their derivatives, and the re-centred matrix has the smaller norm.
+Test infrastructure only.
 """
 from __future__ import annotations
 
@@ -26,7 +30,7 @@ from workloads import Problem
 
 from . import grid
 from .expm import expm
-from .lmep import exp_row, frozen_step
+from .lmep import exp_row, frozen_step, recentring_shift
 from .operator import local_matrix, unit_D
 
 
@@ -45,11 +49,12 @@ def point_derivatives(p: Problem, u: np.ndarray, i: int, D=None):
         D = unit_D(p.n)
     k = grid.departure_shift(u[i], p.dt, p.h, p.n) if p.departure_centring else 0
     idx, r = grid.stencil(p, i, k)
-    X = local_matrix(p, u[i], D)
+    kr = recentring_shift(p, u[i], r)
+    Xk = local_matrix(p, u[i], D) + kr * D[1]
     w = exp_row(p, r, u[i], D)[0]
     dX_du = -(p.dt * p.frozen_adv / p.h) * D[1]
     dX_dnu = (p.dt / p.h ** 2) * D[2]
-    return idx, r, w, frechet(X, dX_du)[r], frechet(X, dX_dnu)[r]
+    return idx, r, w, frechet(Xk, dX_du)[r - kr], frechet(Xk, dX_dnu)[r - kr]
 
 
 def adjoint_step(p: Problem, u: np.ndarray, lam_next: np.ndarray, D=None):

@@ -64,14 +64,13 @@ def test_build_operator(L, H, case):
         k = ogrid.departure_shift(u[i], p.dt, p.h, p.n) if (u is not None and p.departure_centring) else 0
         idx, r = ogrid.stencil(p, i, k)
         assert rw[i] == r
-        assert (st[i] + np.arange(p.n)) % p.N == idx[0] % p.N or p.bc == wl.NEUMANN or True
         X = oop.local_matrix(p, 0.0 if u is None else u[i], D)
         want = oop.augmented_row(X, p.dt, r, n_phi) if n_phi else X
         assert np.max(np.abs(M[i] - want)) <= 1e-14 * max(1.0, np.max(np.abs(want))), i
-    if p.bc == wl.DIRICHLET:
-        for i in range(p.N):
-            k = ogrid.departure_shift(u[i], p.dt, p.h, p.n) if (u is not None and p.departure_centring) else 0
-            assert st[i] == ogrid.stencil(p, i, k)[0][0]
+        if p.bc == wl.DIRICHLET:
+            assert st[i] == idx[0]
+        elif p.bc == wl.PERIODIC:
+            assert st[i] % p.N == idx[0]
 
 
 # ------------------------------------------------------------------ (a4)
@@ -142,7 +141,27 @@ def test_harvest_frozen(L, H, precision, n, cfl, nu):
     for i in range(1, N - 1):
         want[i] = olmep.point_weights(p, u, i, D)[2][0]
     assert np.all(got[0] == 0) and np.all(got[-1] == 0)
-    assert weight_err(got[1:-1], want[1:-1]) <= tol(precision)
+    if nu <= 1e-6 or precision == "mixed":
+        assert weight_err(got[1:-1], want[1:-1]) <= tol(precision)
+        return
+    # As-written viscosity: ||X||_1 reaches ~470 (s = 7 squarings) and FP64 Pade
+    # scaling and squaring -- the oracle's included -- is only good to ~1e-11
+    # there.  Where the two differ by more than 1e-12 the exact rows decide: the
+    # GPU must be at least as accurate as the oracle (within 2x).
+    mp = pytest.importorskip("mpmath")
+    from test_oracle_adjoint_exact import exact_row
+    diff = np.max(np.abs(got - want), axis=1) / np.maximum(np.sum(np.abs(want), axis=1), 1e-300)
+    diff[0] = diff[-1] = 0.0
+    worst = [int(i) for i in np.argsort(-diff)[:12] if diff[i] > 1e-12]
+    e_gpu, e_orc = [], []
+    for i in worst:
+        idx, r = ogrid.stencil(p, i, ogrid.departure_shift(u[i], p.dt, p.h, n))
+        ex = exact_row(n, -p.dt * u[i] / p.h, p.dt * p.c2 / p.h ** 2, r)
+        den = np.sum(np.abs(ex))
+        e_gpu.append(np.max(np.abs(got[i] - ex)) / den)
+        e_orc.append(np.max(np.abs(want[i] - ex)) / den)
+    if worst:
+        assert max(e_gpu) <= max(2 * max(e_orc), 1e-12), (worst, e_gpu, e_orc)
 
 
 # ------------------------------------------------------------------ (a6) stored weights
@@ -289,17 +308,23 @@ def test_adjoint_step(L, H, precision, centring):
     L.lmep_sync_status(H)
     want_lam, want_dnu = oadj.adjoint_step(p, u, lam_next)
     assert rel_linf(lam.cpu().numpy(), want_lam) <= 10 * tol(precision)
-    assert abs(dnu.item() - want_dnu) <= 10 * tol(precision) * max(abs(want_dnu), 1e-30) + 1e-12 * abs(want_dnu)
+    # dJ/dnu is a sum with cancellation: bound its error by the sum of |terms|
+    D = oop.unit_D(p.n)
+    terms = []
+    for i in ogrid.updated_points(p):
+        idx, r, w, dwu, dwnu = oadj.point_derivatives(p, u, i, D)
+        terms.append(lam_next[i] * (dwnu @ u[idx]))
+    assert abs(dnu.item() - want_dnu) <= 10 * tol(precision) * np.sum(np.abs(terms))
 
 
 # ------------------------------------------------------------------ status flags
 def test_nonfinite_is_reported(L, H):
     """The as-written viscosity blows up; the overflow surfaces as LMEP_ERR_NONFINITE."""
-    p = wl.burgers(N=257, n=7, cfl=4.0, nu=1e-3)
-    u = dev(wl.burgers_ic(257, 0))
+    p = wl.burgers(N=65536, n=7, cfl=4.0, nu=1e-3)      # mu = nu dt / h^2 ~ 130
+    u = dev(wl.burgers_ic(p.N, 0))
     work = torch.empty_like(u)
     with pytest.raises(L.LmepError) as e:
-        L.lmep_step(H, grid_of(p), op_of(p), "linear", "none", p.dt, None, u, work, 400, "fp64")
+        L.lmep_step(H, grid_of(p), op_of(p), "linear", "none", p.dt, None, u, work, 300, "fp64")
         L.lmep_sync_status(H)
     assert e.value.status == 3
     L.lmep_sync_status(H)          # flags were cleared
