@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the LMEP hot path on GB300.
+
+Workload (one "step"): one time step of frozen-velocity viscous Burgers on
+[-1, 1] with u = 0 at both walls, N = 65536 points, for each of the nine
+(stencil width n, Courant number) pairs n in {7, 9, 13} x CFL in {1, 2, 4}
+(dt = CFL h / max|u0|), nu = 1e-6 (the stable variant of the stated nu = 1e-3),
+departure-centred windows.  Every point rebuilds and exponentiates its local
+operator at every step (a1-a6 fused in one launch per instance).
+
+value      point-updates/s of the FP32 form (FP32 Pade products and banded
+           apply, FP64 denominator solve and squaring phase), inputs resident.
+fp64       the same for the plain FP64 path.
+e2e        the FP32 form through the public API with host buffers: every step
+           copies the states in from pinned host memory and the result back.
+roofline   the dominant kernel (the n = 13 launches), ALU-bound: achieved
+           FP64-equivalent FLOP/s of the algorithm's own work per launch.
+cpu_baseline  the FP64 oracle on the host cores (spawn pool) on a bounded
+           sample of points of the same step; its outputs also give the
+           stated error of both GPU paths.
+
+--impl reference runs that oracle alone (each step a bounded sample).
+Multi-GPU (torchrun): every rank advances its own independent set of nine
+instances (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "point-updates/s incl. local expm: plain FP64 vs batched FP32 form at stated error"
+UNIT = "point-updates/s"
+N_POINTS = 65536
+NS = (7, 9, 13)
+CFLS = (1.0, 2.0, 4.0)
+NU = 1e-6
+PI_M = {3: 2, 5: 3, 7: 4, 9: 5, 13: 6}          # matrix products of Pade [m/m] (Higham 2005)
+P32_NOMINAL = 152 * 128 * 2 * 2.07e9             # FP32 FMA lanes x 2 x max SM clock
+P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
+
+
+def workload_config(rank_seed: int = 0) -> dict:
+    return {"workload": f"frozen-velocity viscous Burgers, Dirichlet u=0 on [-1,1], N={N_POINTS}, "
+                        f"n in {{7,9,13}} x CFL in {{1,2,4}} (9 instances per step), nu={NU} (stable variant), "
+                        "departure-centred windows, IC -sin(pi x) + 8 seeded Gaussian bumps",
+            "points_per_step": N_POINTS * len(NS) * len(CFLS),
+            "l2": "flushed between timed steps (256 MiB write, untimed)",
+            "seed": rank_seed}
+
+
+def instances(seed: int):
+    import workloads as wl
+    out = []
+    for n in NS:
+        for cfl in CFLS:
+            out.append((n, cfl, wl.burgers(N=N_POINTS, n=n, cfl=cfl, nu=NU, seed=seed)))
+    return out
+
+
+# ------------------------------------------------------------------ oracle leg (CPU)
+def _oracle_points(task):
+    """Worker: oracle frozen-velocity update of the given points (one instance)."""
+    n, cfl, seed, pts = task
+    import numpy as np
+    import workloads as wl
+    from oracle import lmep as olmep, operator as oop
+    p = wl.burgers(N=N_POINTS, n=n, cfl=cfl, nu=NU, seed=seed)
+    u = wl.burgers_ic(N_POINTS, seed)
+    D = oop.unit_D(n)
+    vals = []
+    for i in pts:
+        idx, r, w = olmep.point_weights(p, u, int(i), D)
+        vals.append(float(w[0] @ u[idx]))
+    return np.array(vals)
+
+
+def oracle_pool(cores: int):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores)
+    pool.map(_oracle_points, [(7, 1.0, 0, [1])] * cores)      # warm the workers (imports)
+    return pool
+
+
+def sample_points(per_instance: int, salt: int):
+    import numpy as np
+    rng = np.random.default_rng(1234 + salt)
+    return sorted(set(rng.integers(1, N_POINTS - 1, per_instance).tolist()))
+
+
+def run_oracle_sample(pool, cores: int, seed: int, per_instance: int, salt: int = 0):
+    """Time the oracle on `per_instance` points of each of the nine instances."""
+    tasks = []
+    for n in NS:
+        for cfl in CFLS:
+            pts = sample_points(per_instance, salt + n * 10 + int(cfl))
+            chunk = max(1, math.ceil(len(pts) / cores))
+            for c in range(0, len(pts), chunk):
+                tasks.append((n, cfl, seed, pts[c:c + chunk]))
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_points, tasks)
+    dt = time.perf_counter() - t0
+    npts = sum(len(t[3]) for t in tasks)
+    return tasks, res, npts, dt
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU leg
+def flops_model(n: int, stats, fp32_form: bool):
+    """Algorithmic FLOPs of one point-update given (m, s, a): (FP32 part, FP64 part)."""
+    import numpy as np
+    m, s, a = stats[:, 0], stats[:, 1], stats[:, 2]
+    d = float(n)
+    prod = np.vectorize(lambda mm: PI_M.get(int(mm), 6))(m) * 2 * d ** 3
+    solve = (8.0 / 3.0) * d ** 3
+    sq = a * 2 * d ** 3 + ((2.0 ** (s - a)) - 1) * 2 * d * d
+    apply_ = 2 * d
+    if fp32_form:
+        return float(np.sum(prod + apply_)), float(np.sum(solve + sq))
+    return 0.0, float(np.sum(prod + apply_ + solve + sq))
+
+
+def gpu_leg(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    import workloads as wl
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    h = L.Handle()
+    seed = rank
+    insts = instances(seed)
+    u0 = {}
+    for n, cfl, p in insts:
+        u0[(n, cfl)] = wl.burgers_ic(N_POINTS, seed)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def grid_op(p):
+        return (L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True),
+                L.Operator(c2=p.c2, frozen_adv=1.0))
+
+    results = {}
+    for prec in ("mixed", "fp64"):
+        dt_ = L.state_dtype(prec)
+        bufs = {}
+        for n, cfl, p in insts:
+            u = torch.tensor(u0[(n, cfl)], dtype=dt_, device=dev)
+            bufs[(n, cfl)] = (u, torch.empty_like(u))
+        # stats (m, s, a) of every point at the initial state, from the kernel itself
+        stats = {}
+        for n, cfl, p in insts:
+            g, op = grid_op(p)
+            st = torch.zeros(N_POINTS, 3, dtype=torch.int32, device=dev)
+            L.lmep_frozen_stats(h, g, op, p.dt, bufs[(n, cfl)][0], st, prec)
+            stats[(n, cfl)] = st.cpu().numpy()[1:-1]
+        # first step from u0 (kept for the stated error)
+        first = {}
+        for n, cfl, p in insts:
+            g, op = grid_op(p)
+            u, w = bufs[(n, cfl)]
+            v = u.clone()
+            L.lmep_step(h, g, op, "linear", "none", p.dt, None, v, w, 1, prec)
+            first[(n, cfl)] = v.cpu().numpy()
+        L.lmep_sync_status(h)
+
+        def one_step(ev=None):
+            for n, cfl, p in insts:
+                g, op = grid_op(p)
+                u, w = bufs[(n, cfl)]
+                if ev is not None and n == 13:
+                    ev[(n, cfl)][0].record(stream)
+                L.lmep_step(h, g, op, "linear", "none", p.dt, None, u, w, 1, prec)
+                if ev is not None and n == 13:
+                    ev[(n, cfl)][1].record(stream)
+
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        step_ms = []
+        kern_ms = {k: [] for k in u0 if k[0] == 13}
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in kern_ms}
+            a.record(stream)
+            one_step(ev)
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+            for k, (e0, e1) in ev.items():
+                kern_ms[k].append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        L.lmep_sync_status(h)
+        total_ms = float(sum(step_ms))
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        pts = N_POINTS * len(insts) * args.steps * world
+        # roofline of the n = 13 launches
+        f32 = f64 = 0.0
+        t13 = 0.0
+        for k, times in kern_ms.items():
+            a32, a64 = flops_model(13, stats[k], prec == "mixed")
+            f32 += a32 * len(times)
+            f64 += a64 * len(times)
+            t13 += sum(times) * 1e-3
+        results[prec] = {"value": pts / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
+                         "first": first, "clocks": clk, "f32": f32, "f64": f64, "t13": t13,
+                         "launches13": sum(len(v) for v in kern_ms.values()),
+                         "stats": {f"n{k[0]}_cfl{int(k[1])}": {
+                             "m": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 0], return_counts=True))},
+                             "s": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 1], return_counts=True))}}
+                             for k in stats}}
+    # e2e (FP32 form): host buffers through the public API, copies inside the timed region
+    dt_ = torch.float32
+    host_in = {k: torch.tensor(v, dtype=dt_).pin_memory() for k, v in u0.items()}
+    host_out = {k: torch.empty(N_POINTS, dtype=dt_).pin_memory() for k in u0}
+    dbuf = {k: (torch.empty(N_POINTS, dtype=dt_, device=dev), torch.empty(N_POINTS, dtype=dt_, device=dev))
+            for k in u0}
+    e2e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for it in range(e2e_steps + 1):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for n, cfl, p in insts:
+            g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True)
+            op = L.Operator(c2=p.c2, frozen_adv=1.0)
+            u, w = dbuf[(n, cfl)]
+            u.copy_(host_in[(n, cfl)], non_blocking=True)
+            L.lmep_step(h, g, op, "linear", "none", p.dt, None, u, w, 1, "mixed")
+            host_out[(n, cfl)].copy_(u, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if it > 0:                      # the first iteration is a warm-up
+            e2e_ms.append(a.elapsed_time(b))
+        for k in u0:                    # next step's input is this step's output
+            host_in[k].copy_(host_out[k])
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    results["e2e"] = {"value": N_POINTS * len(insts) * e2e_steps * world / (e2e_total * 1e-3), "unit": UNIT,
+                      "h2d_bytes_per_step": N_POINTS * len(insts) * 4,
+                      "d2h_bytes_per_step": N_POINTS * len(insts) * 4}
+    results["fma_peak_fp64"] = L.lmep_fma_peak("fp64")
+    results["fma_peak_fp32"] = L.lmep_fma_peak("mixed")
+    h.close()
+    return results
+
+
+def stated_error(results, tasks, res):
+    import numpy as np
+    import workloads as wl
+    out = {}
+    scale = max(float(np.max(np.abs(wl.burgers_ic(N_POINTS, 0)))), 1e-300)
+    for prec in ("mixed", "fp64"):
+        worst = 0.0
+        for (n, cfl, seed, pts), vals in zip(tasks, res):
+            got = results[prec]["first"][(n, cfl)][pts]
+            worst = max(worst, float(np.max(np.abs(got - vals))) / scale)
+        out["fp32_form" if prec == "mixed" else "fp64"] = worst
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle points per instance (cpu_baseline)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    cores = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        pool = oracle_pool(cores)
+        per = 64
+        for w in range(args.warmup):
+            run_oracle_sample(pool, cores, 0, 8, salt=1000 + w)
+        total, npts = 0.0, 0
+        for k in range(args.steps):
+            _, _, np_, dt = run_oracle_sample(pool, cores, 0, per, salt=k)
+            total += dt
+            npts += np_
+        pool.close()
+        v = npts / total
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload_config(0),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"{per} random interior points of each of the 9 instances per step"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    # the oracle pool is spawned before the first GPU call
+    pool = oracle_pool(cores) if rank == 0 and world == 1 else None
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = gpu_leg(args, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    err = None
+    if pool is not None:
+        tasks, vals, npts, dt = run_oracle_sample(pool, cores, 0, args.cpu_sample)
+        pool.close()
+        cpu = {"value": npts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} random interior points of each of the 9 instances, one step "
+                         f"({npts} point-updates, {dt:.1f} s)"}
+        err = stated_error(res, tasks, vals)
+    m = res["mixed"]
+    t13 = m["t13"]
+    p64 = P64_NOMINAL
+    achieved = (m["f64"] + m["f32"] * (p64 / P32_NOMINAL)) / t13
+    line = {
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64 (FP32 Pade products and banded apply; FP64 solve and squaring)",
+        "data": "synthetic", "config": workload_config(0),
+        "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"], "dtype": "f64"},
+        "error": {"vs": "FP64 oracle, one step from the initial state, sampled points (cpu_baseline sample)",
+                  "rel_linf": err},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / p64, "traffic": None,
+                     "kernel": "k_warp<13,float> (frozen-velocity fused step, n = 13)",
+                     "note": "FP64-equivalent rate (F64 + F32 * P64/P32) / t of the algorithm's own FLOPs; "
+                             "peak = GB300 nominal FP64; see measured FMA-chain peaks",
+                     "f64_tflops": m["f64"] / t13 / 1e12, "f32_tflops": m["f32"] / t13 / 1e12,
+                     "measured_fma_peak_fp64_tflops": res["fma_peak_fp64"] / 1e12,
+                     "measured_fma_peak_fp32_tflops": res["fma_peak_fp32"] / 1e12,
+                     "launches": m["launches13"], "avg_launch_ms": 1e3 * t13 / m["launches13"]},
+        "fp64_roofline": {"achieved": res["fp64"]["f64"] / res["fp64"]["t13"] / 1e12, "peak": p64 / 1e12,
+                          "unit": "TFLOP/s", "frac": res["fp64"]["f64"] / res["fp64"]["t13"] / p64},
+        "cpu_baseline": cpu,
+        "e2e": res["e2e"],
+        "gpu_launches": len(NS) * len(CFLS) * args.steps,
+        "clocks": m["clocks"],
+        "pade_ms_histogram": m["stats"],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

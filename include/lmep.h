@@ -188,6 +188,15 @@ LMEP_API lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const
                               double* dnu_dev, void* scratch_dev, size_t scratch_bytes,
                               int32_t precision, void* stream);
 
+/* Diagnostics of the frozen-velocity path: for every point i write
+ * stats_dev[3 i .. 3 i + 2] = (Pade degree m, squarings s, full squarings a)
+ * exactly as the fused step chooses them for state u_dev (the remaining
+ * 2^(s-a) - 1 squaring factors act on the harvested row only).  Runs the
+ * frozen-velocity kernel without writing weights.  Dirichlet wall points are
+ * left untouched.  u_dev: state dtype of `precision`; stats_dev: int32[N][3]. */
+LMEP_API lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                                       const void* u_dev, int32_t* stats_dev, int32_t precision, void* stream);
+
 /* Synchronise `stream`, read and clear the device status flags.
  * Returns LMEP_ERR_NONFINITE if any kernel produced Inf/NaN since the last call. */
 LMEP_API lmep_status lmep_sync_status(lmep_handle* h, void* stream);

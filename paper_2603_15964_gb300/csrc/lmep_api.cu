@@ -421,6 +421,22 @@ lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_ope
   return LMEP_OK;
 }
 
+lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                              const void* u_dev, int32_t* stats_dev, int32_t precision, void* stream) {
+  if (!h || !op || !u_dev || !stats_dev) return fail(LMEP_ERR_INVALID, "NULL argument");
+  lmep_status st = check_grid(g, 0);
+  if (st != LMEP_OK) return st;
+  st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "lmep_frozen_stats needs a frozen operator");
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann needs N >= 2n");
+  CK(lmep::launch_frozen(make_params(g, op, dt, 0), u_dev, nullptr, false, precision == LMEP_PREC_MIXED, h->flags,
+                         S(stream), stats_dev),
+     "frozen_stats");
+  return LMEP_OK;
+}
+
 lmep_status lmep_sync_status(lmep_handle* h, void* stream) {
   if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
   CK(cudaStreamSynchronize(S(stream)), "cudaStreamSynchronize");

@@ -431,7 +431,7 @@ __device__ __forceinline__ void rows_times(double* V, const double* R, int ldr, 
 // whole exponential into E (stride lde) when full == true.  ms receives (m, s).
 template <int D, typename PT>
 __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
-                          double* E, int lde, int* m_out, int* s_out) {
+                          double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr) {
   constexpr int S = Slots<D>::S;
   const Slots<D> sl(lane);
   // ||X||_1 = max column sum
@@ -509,6 +509,7 @@ __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* row
   __syncwarp();
   if (m_out) *m_out = m;
   if (s_out) *s_out = s;
+  if (a_out) *a_out = a;
 }
 
 }  // namespace lmep

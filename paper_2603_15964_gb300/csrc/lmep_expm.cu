@@ -134,7 +134,7 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
 }
 
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
-                          unsigned* flags, cudaStream_t s) {
+                          unsigned* flags, cudaStream_t s, int32_t* stats) {
   if (p.n_phi != 0) return cudaErrorInvalidValue;
   WarpJob job{};
   job.mode = fused ? MODE_FROZEN_STEP : MODE_FROZEN_W;
@@ -143,6 +143,7 @@ cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused
   job.u = u;
   job.out = out;
   job.flags = flags;
+  job.ms = stats;
   return mixed ? warp_job_f32(p.n, job, s) : warp_job_f64(p.n, job, s);
 }
 

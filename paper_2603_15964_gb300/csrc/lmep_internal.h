@@ -34,7 +34,7 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
                                  bool mixed, cudaStream_t s);
 // Frozen velocity: fused == false writes W[N][n]; fused == true writes u_out.
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
-                          unsigned* flags, cudaStream_t s);
+                          unsigned* flags, cudaStream_t s, int32_t* stats = nullptr);
 
 // ---- banded apply (lmep_apply.cu)
 struct Instance {

@@ -33,7 +33,7 @@ struct WarpJob {
   int64_t items;        // matrices, (instance, row) pairs or points
   const double* A;      // MODE_FULL input
   double* E;            // MODE_FULL output
-  int32_t* ms;          // MODE_FULL (m, s), nullable
+  int32_t* ms;          // MODE_FULL (m, s); frozen modes (m, s, a); nullable
   const double* h_inst; // MODE_CONST per-instance spacing, nullable
   const void* u;        // frozen velocities / state
   void* out;            // weights or next state
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_warp(WarpJob job) {
   ST* out = static_cast<ST*>(job.out);
   const bool dir = p.bc == BC_DIRICHLET;
   const bool frozen = mode == MODE_FROZEN_W || mode == MODE_FROZEN_STEP;
-  if (frozen && dir && blockIdx.x == 0 && warp == 0) {
+  if (frozen && dir && out && blockIdx.x == 0 && warp == 0) {
     if (mode == MODE_FROZEN_STEP) {
       if (lane == 0) out[0] = ST(p.bc_lo);
       if (lane == 1) out[p.N - 1] = ST(p.bc_hi);
@@ -151,7 +151,17 @@ __global__ void __launch_bounds__(32 * WARPS) k_warp(WarpJob job) {
                 p.dt * p.c3 / (p.h * p.h * p.h), lane);
     __syncwarp();
     const int hr = r - kr;
-    warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, nullptr, nullptr);
+    int m_, s_, a_;
+    warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, &m_, &s_, &a_);
+    if (job.ms && lane == 0) {
+      job.ms[3 * i] = m_;
+      job.ms[3 * i + 1] = s_;
+      job.ms[3 * i + 2] = a_;
+    }
+    if (!out) {
+      __syncwarp();
+      continue;
+    }
     if (mode == MODE_FROZEN_STEP) {
       ST acc = ST(0);
       if (lane < n) acc = ST(w.V[lane]) * u[grid_index(st + lane, p.N, p.bc)];
