@@ -3,14 +3,22 @@
 // One warp owns one small matrix (dimension d <= 16) in shared memory:
 //   * Fornberg derivative weights on the integer window nodes (Sec. 2.1 step 1),
 //   * stencil window / harvest row selection (Sec. 2.1 steps 1 and 3),
-//   * Pade [m/m] scaling and squaring exp(X) (Sec. 2.1 step 2; Higham 2005,
-//     "The scaling and squaring method for the matrix exponential revisited",
-//     Algorithm 2.3, degree choice by ||X||_1 against theta_m of its Table 2.3),
-//     with the polynomial products in PT (double, or float for the FP32 form),
-//     the denominator solve by Gauss-Jordan elimination with partial pivoting
-//     in FP64, and the squaring phase in FP64.  Because only a few rows of
-//     exp(X) are harvested, the last 2^b factors of the squaring phase are
-//     applied to those rows only (row vector times R, repeated).
+//   * Pade [m/m] scaling and squaring exp(X) (Sec. 2.1 step 2), with the
+//     polynomial products in PT (double, or float for the FP32 form), the
+//     denominator solve by Gauss-Jordan elimination with partial pivoting in
+//     FP64, and the squaring phase in FP64.
+//     Degree: m in {3,5,7,9} when ||X||_1 <= theta_m (Higham 2005,
+//     Algorithm 2.3, theta_m of its Table 2.3), else m = 13.  Scaling for
+//     m = 13: Al-Mohy & Higham, "A new scaling and squaring algorithm for the
+//     matrix exponential", SIMAX 31(3), 2009: s from
+//     alpha = min_{p<=5} max(||X^p||^(1/p), ||X^(p+1)||^(1/(p+1))) (their
+//     Thm. 4.2; the norms are computed exactly from the powers), plus their
+//     correction ell for non-normal X from ||(|X_s|)^27||_1.  The local LMEP
+//     operators are nilpotent up to rounding, so alpha << ||X||_1 and s is
+//     usually 0.  Because only a few rows of exp(X) are harvested, the last
+//     2^b factors of the squaring phase act on those rows only, and with
+//     s = 0 a single row is obtained from one transposed solve y^T Q = e_r^T,
+//     w = y^T P.
 #pragma once
 
 #include <cstdint>
@@ -225,25 +233,11 @@ __device__ __forceinline__ void lincomb(T (&v)[Slots<D>::S], const Slots<D>& sl,
   }
 }
 
-// Pade degree m and squarings s from ||X||_1 (Higham 2005, Algorithm 2.3).
-__device__ __forceinline__ void choose_ms(double nrm, int& m, int& s) {
-  s = 0;
-  if (nrm <= THETA3) m = 3;
-  else if (nrm <= THETA5) m = 5;
-  else if (nrm <= THETA7) m = 7;
-  else if (nrm <= THETA9) m = 9;
-  else {
-    m = 13;
-    // smallest s >= 0 with nrm / 2^s <= theta_13 (exact power-of-two test)
-    double t = nrm;
-    while (t > THETA13 && s < 1023) { t *= 0.5; ++s; }
-  }
-}
-
-// Odd part U and even part V of p_m(X) for the lane's slots; X is PRD slot 0.
-// Products follow Higham (2005) eqs. (2.10)-(2.11); the degree only changes
-// which powers exist and which coefficients multiply them, so every degree
-// shares the same product call sites.  Uses PRD slots 1..4.
+// Odd part U and even part V of p_m(X) for the lane's slots; X is PRD slot 0
+// and X^2, X^4, X^6 (as far as m needs them) are in slots 1..3.  Products
+// follow Higham (2005) eqs. (2.10)-(2.11); the degree only changes which
+// powers exist and which coefficients multiply them, so every degree shares
+// the same product call sites.  Uses PRD slot 4 as scratch.
 template <int D, typename PT>
 __device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& sl, PT (&U)[Slots<D>::S],
                                         PT (&V)[Slots<D>::S]) {
@@ -255,6 +249,7 @@ __device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& 
   PT* T = w.M(4);
   PT acc[S], A8[S];
   PT b[14];
+  (void)A4;
 #pragma unroll
   for (int j = 0; j < 14; ++j) b[j] = PT(0);
   switch (m) {
@@ -278,20 +273,8 @@ __device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& 
 #pragma unroll
       for (int j = 0; j <= 13; ++j) b[j] = PT(pade_b(13, j));
   }
-  // powers X^2, X^4, X^6 (and X^8 in registers for m = 9)
-  mm_slots<D, LD, LD>(X, X, acc, sl);
-  store_slots<D>(A2, acc, sl);
-  __syncwarp();
-  if (m >= 5) {
-    mm_slots<D, LD, LD>(A2, A2, acc, sl);
-    store_slots<D>(A4, acc, sl);
-    __syncwarp();
-  }
-  if (m >= 7) {
-    mm_slots<D, LD, LD>(A4, A2, acc, sl);
-    store_slots<D>(A6, acc, sl);
-    __syncwarp();
-  }
+  // X^2, X^4, X^6 are already in PRD slots 1..3 (see powers_and_scaling);
+  // X^8 for m = 9 in registers
   if (m == 9) mm_slots<D, LD, LD>(A6, A2, A8, sl);
   const PT* P2 = A2;
   const PT* P4 = m >= 5 ? A4 : nullptr;
@@ -340,7 +323,7 @@ __device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& 
 // partial pivoting (FP64).  On return G[:, D:2D] holds R.  Pivot magnitudes
 // are compared as IEEE bit patterns (monotonic for non-negative doubles).
 template <int D>
-__device__ void gauss_jordan(double* G, int lane) {
+__device__ void gauss_jordan(double* G, int lane, int ncols = 2 * D) {
   for (int k = 0; k < D; ++k) {
     long long key = -1;
     int idx = k;
@@ -358,7 +341,7 @@ __device__ void gauss_jordan(double* G, int lane) {
       }
     }
     if (idx != k) {
-      for (int j = k + lane; j < 2 * D; j += 32) {
+      for (int j = k + lane; j < ncols; j += 32) {
         const double a = G[k * LDG + j];
         G[k * LDG + j] = G[idx * LDG + j];
         G[idx * LDG + j] = a;
@@ -366,9 +349,9 @@ __device__ void gauss_jordan(double* G, int lane) {
     }
     __syncwarp();
     const double inv = __drcp_rn(G[k * LDG + k]);
-    for (int j = k + 1 + lane; j < 2 * D; j += 32) G[k * LDG + j] *= inv;
+    for (int j = k + 1 + lane; j < ncols; j += 32) G[k * LDG + j] *= inv;
     __syncwarp();
-    const int nc = 2 * D - k - 1;
+    const int nc = ncols - k - 1;
     const int tot = (D - 1) * nc;
     const float rnc = 1.0f / float(nc);
     for (int e = lane; e < tot; e += 32) {
@@ -426,85 +409,225 @@ __device__ __forceinline__ void rows_times(double* V, const double* R, int ldr, 
   __syncwarp();
 }
 
-// exp(X) for X = w.X64 (D x D, double).  Writes the harvested rows
-// rows[0..nrows) into w.V[q*DMAX + j] (double) when full == false, or the
-// whole exponential into E (stride lde) when full == true.  ms receives (m, s).
-template <int D, typename PT>
-__device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
-                          double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr) {
-  constexpr int S = Slots<D>::S;
-  const Slots<D> sl(lane);
-  // ||X||_1 = max column sum
+// 1-norm (max column sum) of a D x D matrix in shared memory, all lanes.
+template <int D, typename T>
+__device__ __forceinline__ double norm1_smem(const T* M, int lane) {
   double cs = 0.0;
   if (lane < D) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) cs += fabs(w.X64[i * LD + lane]);
+    for (int i = 0; i < D; ++i) cs += fabs(double(M[i * LD + lane]));
   }
-  const double nrm = warp_max(cs);
-  int m, s;
-  choose_ms(nrm, m, s);
-  const double sc = ldexp(1.0, -s);
+  return warp_max(cs);
+}
+
+// Leading coefficient |c_{2m+1}| = (m!)^2 / ((2m)! (2m+1)!) of the backward
+// error series of the [13/13] Pade approximant (Al-Mohy & Higham 2009).
+__host__ __device__ constexpr double pade13_c27() {
+  double c = 1.0;
+  for (int k = 1; k <= 13; ++k) c *= double(k) / double(13 + k);     // 13! / (26! / 13!)
+  for (int k = 1; k <= 27; ++k) c /= double(k);                      // / 27!
+  for (int k = 1; k <= 13; ++k) c *= double(k);                      // * 13!
+  return c;
+}
+
+// Powers X^2, X^4, X^6 into PRD slots 1..3 (PT) from X in slot 0, degree m
+// and scaling s.  m = 13 uses the Al-Mohy & Higham (2009) choice of s (see the
+// file header); the powers are then scaled by exact powers of two.
+template <int D, typename PT>
+__device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane, double nrm, int& m, int& s) {
+  constexpr int S = Slots<D>::S;
+  PT* X = w.M(0);
+  PT* A2 = w.M(1);
+  PT* A4 = w.M(2);
+  PT* A6 = w.M(3);
+  PT* T = w.M(4);
+  PT acc[S];
+  s = 0;
+  if (nrm <= THETA3) m = 3;
+  else if (nrm <= THETA5) m = 5;
+  else if (nrm <= THETA7) m = 7;
+  else if (nrm <= THETA9) m = 9;
+  else m = 13;
+  // Norms of powers overflow FP32 for very large ||X||: there, and for
+  // non-finite input, scale by the norm first (Higham 2005) and stop.
+  const bool by_norm = m == 13 && !(nrm <= 8192.0);
+  if (by_norm) {
+    double t = nrm;
+    while (t > THETA13 && s < 1023) { t *= 0.5; ++s; }
+    const PT sc = PT(ldexp(1.0, -s));
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+      if (sl.ok[q]) X[sl.i[q] * LD + sl.j[q]] *= sc;
+    __syncwarp();
+  }
+  mm_slots<D, LD, LD>(X, X, acc, sl);
+  store_slots<D>(A2, acc, sl);
+  __syncwarp();
+  if (m >= 5) {
+    mm_slots<D, LD, LD>(A2, A2, acc, sl);
+    store_slots<D>(A4, acc, sl);
+    __syncwarp();
+  }
+  if (m >= 7) {
+    mm_slots<D, LD, LD>(A4, A2, acc, sl);
+    store_slots<D>(A6, acc, sl);
+    __syncwarp();
+  }
+  if (m != 13 || by_norm) return;
+  // d_p = ||X^p||^(1/p), p = 1..6, with X^3 = X^2 X and X^5 = X^4 X through T
+  double lg[7];
+  lg[1] = log2(nrm);
+  lg[2] = log2(norm1_smem<D>(A2, lane)) / 2.0;
+  lg[4] = log2(norm1_smem<D>(A4, lane)) / 4.0;
+  lg[6] = log2(norm1_smem<D>(A6, lane)) / 6.0;
+  mm_slots<D, LD, LD>(A2, X, acc, sl);
+  store_slots<D>(T, acc, sl);
+  __syncwarp();
+  lg[3] = log2(norm1_smem<D>(T, lane)) / 3.0;
+  __syncwarp();
+  mm_slots<D, LD, LD>(A4, X, acc, sl);
+  __syncwarp();
+  store_slots<D>(T, acc, sl);
+  __syncwarp();
+  lg[5] = log2(norm1_smem<D>(T, lane)) / 5.0;
+  double la = lg[1];  // log2 alpha = min_p max(lg_p, lg_{p+1})
+#pragma unroll
+  for (int p = 1; p <= 5; ++p) la = fmin(la, fmax(lg[p], lg[p + 1]));
+  const double lt = log2(THETA13);
+  int s0 = la > lt ? int(ceil(la - lt)) : 0;
+  // ell: ||(|X_s|)^27||_1 = max_j (1^T |X|^27)_j / 2^(27 s), by a normalised
+  // row-vector iteration on |X| (FP32 is ample for an exponent estimate).
+  __syncwarp();
+  float v = lane < D ? 1.0f : 0.0f;
+  float l27 = 0.0f;
+  for (int it = 0; it < 27; ++it) {
+    float acc1 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float xkj = lane < D ? fabsf(float(X[k * LD + lane])) : 0.0f;
+      acc1 = fmaf(__shfl_sync(FULL, v, k), xkj, acc1);
+    }
+    float mx = acc1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    if (!(mx > 0.0f)) { l27 = -1e30f; break; }
+    l27 += log2f(mx);
+    v = acc1 / mx;
+  }
+  // ell = max(0, ceil(log2(|c27| ||(|X_s|)^27|| / ||X_s|| / u) / 26)), u = 2^-53
+  const double la27 = log2(pade13_c27()) + double(l27) - 27.0 * s0 - (lg[1] - s0);
+  int ell = int(ceil((la27 + 53.0) / 26.0));
+  if (!(ell > 0)) ell = 0;
+  s = s0 + ell;
+  if (s > 0) {
+    const PT c1 = PT(ldexp(1.0, -s)), c2 = PT(ldexp(1.0, -2 * s)), c4 = PT(ldexp(1.0, -4 * s)),
+             c6 = PT(ldexp(1.0, -6 * s));
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      if (sl.ok[q]) {
+        const int o = sl.i[q] * LD + sl.j[q];
+        X[o] *= c1;
+        A2[o] *= c2;
+        A4[o] *= c4;
+        A6[o] *= c6;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// exp(X) for X = w.X64 (D x D, double).  Writes the harvested rows
+// rows[0..nrows) into w.V[q*DMAX + j] (double) when full == false, or the
+// whole exponential into E (stride lde) when full == true.  m_out, s_out and
+// a_out receive the Pade degree, the squarings and the full squarings.
+template <int D, typename PT>
+__device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
+                                       double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr) {
+  constexpr int S = Slots<D>::S;
+  const Slots<D> sl(lane);
+  const double nrm = norm1_smem<D>(w.X64, lane);
   PT* X = w.M(0);
 #pragma unroll
   for (int t = 0; t < S; ++t)
-    if (sl.ok[t]) X[sl.i[t] * LD + sl.j[t]] = PT(w.X64[sl.i[t] * LD + sl.j[t]] * sc);
+    if (sl.ok[t]) X[sl.i[t] * LD + sl.j[t]] = PT(w.X64[sl.i[t] * LD + sl.j[t]]);
   __syncwarp();
+  int m, s;
+  powers_and_scaling<D, PT>(w, sl, lane, nrm, m, s);
   PT U[S], V[S];
   pade_uv<D, PT>(w, m, sl, U, V);
-  // [Q | P] = [V - U | V + U] in FP64
-#pragma unroll
-  for (int t = 0; t < S; ++t) {
-    if (sl.ok[t]) {
-      const double u = double(U[t]), v = double(V[t]);
-      w.G[sl.i[t] * LDG + sl.j[t]] = v - u;
-      w.G[sl.i[t] * LDG + D + sl.j[t]] = v + u;
-    }
-  }
-  __syncwarp();
-  gauss_jordan<D>(w.G, lane);
-  // squaring phase in FP64: R = G[:, D:2D] copied to R1, full squarings
-  // ping-pong between R1 and R2, then the remaining 2^b factors are applied
-  // to the harvested rows only.
-#pragma unroll
-  for (int t = 0; t < S; ++t)
-    if (sl.ok[t]) w.R1[sl.i[t] * LD + sl.j[t]] = w.G[sl.i[t] * LDG + D + sl.j[t]];
-  __syncwarp();
   int a = s;
-  if (!full) {
-    // a full squarings + 2^(s-a) - 1 row products, minimising FP64 instructions
-    const int cost_full = S * D;
-    const int cost_vec = nrows == 1 ? (D + 1) / 2 + 1 : D * ((nrows * D + 31) / 32);
-    // at most 2^6 - 1 row products; larger s always squares in full
-    int best = 1 << 30;
-    for (int aa = (s > 6 ? s - 6 : 0); aa <= s; ++aa) {
-      const int c = aa * cost_full + ((1 << (s - aa)) - 1) * cost_vec;
-      if (c < best) { best = c; a = aa; }
+  if (!full && s == 0 && nrows == 1) {
+    // one row of Q^-1 P: y^T Q = e_r^T (Gauss-Jordan on [Q^T | e_r]), w = y^T P
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      if (sl.ok[t]) {
+        const double u = double(U[t]), v = double(V[t]);
+        w.G[sl.j[t] * LDG + sl.i[t]] = v - u;
+        w.R1[sl.i[t] * LD + sl.j[t]] = v + u;
+      }
     }
-  }
-  double* R = w.R1;
-  double* Rn = w.R2;
-  for (int q = 0; q < a; ++q) {
-    double acc[S];
-    mm_slots<D, LD, LD>(R, R, acc, sl);
-#pragma unroll
-    for (int t = 0; t < S; ++t)
-      if (sl.ok[t]) Rn[sl.i[t] * LD + sl.j[t]] = acc[t];
+    if (lane < D) w.G[lane * LDG + D] = lane == rows[0] ? 1.0 : 0.0;
     __syncwarp();
-    double* tmp = R;
-    R = Rn;
-    Rn = tmp;
-  }
-  if (full) {
-#pragma unroll
-    for (int t = 0; t < S; ++t)
-      if (sl.ok[t]) E[sl.i[t] * lde + sl.j[t]] = R[sl.i[t] * LD + sl.j[t]];
+    gauss_jordan<D>(w.G, lane, D + 1);
+    if (lane < D) w.V[lane] = w.G[lane * LDG + D];
+    __syncwarp();
+    rows_times<D>(w.V, w.R1, LD, 1, lane);
+    a = 0;
   } else {
-    for (int o = lane; o < nrows * D; o += 32) {
-      const int q = o / D, j = o - (o / D) * D;
-      w.V[q * DMAX + j] = R[rows[q] * LD + j];
+    // [Q | P] = [V - U | V + U] in FP64
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      if (sl.ok[t]) {
+        const double u = double(U[t]), v = double(V[t]);
+        w.G[sl.i[t] * LDG + sl.j[t]] = v - u;
+        w.G[sl.i[t] * LDG + D + sl.j[t]] = v + u;
+      }
     }
     __syncwarp();
-    for (int q = 0; q < (1 << (s - a)) - 1; ++q) rows_times<D>(w.V, R, LD, nrows, lane);
+    gauss_jordan<D>(w.G, lane);
+    // squaring phase in FP64: R = G[:, D:2D] copied to R1, full squarings
+    // ping-pong between R1 and R2, then the remaining 2^b factors act on the
+    // harvested rows only.
+#pragma unroll
+    for (int t = 0; t < S; ++t)
+      if (sl.ok[t]) w.R1[sl.i[t] * LD + sl.j[t]] = w.G[sl.i[t] * LDG + D + sl.j[t]];
+    __syncwarp();
+    if (!full) {
+      // a full squarings + 2^(s-a) - 1 row products, minimising FP64 instructions;
+      // at most 2^6 - 1 row products, larger s always squares in full
+      const int cost_full = S * D;
+      const int cost_vec = nrows == 1 ? (D + 1) / 2 + 1 : D * ((nrows * D + 31) / 32);
+      int best = 1 << 30;
+      for (int aa = (s > 6 ? s - 6 : 0); aa <= s; ++aa) {
+        const int c = aa * cost_full + ((1 << (s - aa)) - 1) * cost_vec;
+        if (c < best) { best = c; a = aa; }
+      }
+    }
+    double* R = w.R1;
+    double* Rn = w.R2;
+    for (int q = 0; q < a; ++q) {
+      double acc[S];
+      mm_slots<D, LD, LD>(R, R, acc, sl);
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        if (sl.ok[t]) Rn[sl.i[t] * LD + sl.j[t]] = acc[t];
+      __syncwarp();
+      double* tmp = R;
+      R = Rn;
+      Rn = tmp;
+    }
+    if (full) {
+#pragma unroll
+      for (int t = 0; t < S; ++t)
+        if (sl.ok[t]) E[sl.i[t] * lde + sl.j[t]] = R[sl.i[t] * LD + sl.j[t]];
+    } else {
+      for (int o = lane; o < nrows * D; o += 32) {
+        const int q = o / D, j = o - (o / D) * D;
+        w.V[q * DMAX + j] = R[rows[q] * LD + j];
+      }
+      __syncwarp();
+      for (int q = 0; q < (1 << (s - a)) - 1; ++q) rows_times<D>(w.V, R, LD, nrows, lane);
+    }
   }
   __syncwarp();
   if (m_out) *m_out = m;

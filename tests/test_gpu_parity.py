@@ -91,7 +91,9 @@ def test_expm_batched(L, H, precision, d):
     E, ms = E.cpu().numpy(), ms.cpu().numpy()
     for q in range(len(A)):
         want, m, s = oexpm.expm(A[q], return_ms=True)
-        assert (ms[q, 0], ms[q, 1]) == (m, s)
+        # same degree rule; the GPU scales m = 13 by Al-Mohy & Higham (2009), the
+        # oracle by Higham (2005), so only the degree is compared exactly
+        assert ms[q, 0] == m
         err = np.max(np.abs(E[q] - want)) / np.max(np.abs(want))
         # conditioning of exp grows with the norm: allow the FP64 oracle's own growth
         assert err <= tol(precision) * max(1.0, oexpm.norm1(A[q]) / 5.0), (q, m, s, err)
