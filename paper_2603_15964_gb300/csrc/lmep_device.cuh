@@ -409,6 +409,31 @@ __device__ __forceinline__ void rows_times(double* V, const double* R, int ldr, 
   __syncwarp();
 }
 
+// |x| as a float from the top word of a double with integer operations only
+// (exponent rebias, mantissa truncated to 20 bits; relative error < 2^-20).
+// Used where only a magnitude estimate is needed, to keep the FP64 pipe free.
+__device__ __forceinline__ float approx_abs_f32(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __int_as_float((e << 23) | ((hi & 0xfffff) << 3));
+}
+__device__ __forceinline__ float approx_abs_f32(float x) { return fabsf(x); }
+
+// log2 of the 1-norm (max column sum) of a D x D matrix, FP32 estimate, all lanes.
+template <int D, typename T>
+__device__ __forceinline__ float log2_norm1_est(const T* M, int lane) {
+  float cs = 0.0f;
+  if (lane < D) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) cs += approx_abs_f32(M[i * LD + lane]);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(FULL, cs, o));
+  return log2f(cs);
+}
+
 // 1-norm (max column sum) of a D x D matrix in shared memory, all lanes.
 template <int D, typename T>
 __device__ __forceinline__ double norm1_smem(const T* M, int lane) {
@@ -418,16 +443,6 @@ __device__ __forceinline__ double norm1_smem(const T* M, int lane) {
     for (int i = 0; i < D; ++i) cs += fabs(double(M[i * LD + lane]));
   }
   return warp_max(cs);
-}
-
-// Leading coefficient |c_{2m+1}| = (m!)^2 / ((2m)! (2m+1)!) of the backward
-// error series of the [13/13] Pade approximant (Al-Mohy & Higham 2009).
-__host__ __device__ constexpr double pade13_c27() {
-  double c = 1.0;
-  for (int k = 1; k <= 13; ++k) c *= double(k) / double(13 + k);     // 13! / (26! / 13!)
-  for (int k = 1; k <= 27; ++k) c /= double(k);                      // / 27!
-  for (int k = 1; k <= 13; ++k) c *= double(k);                      // * 13!
-  return c;
 }
 
 // Powers X^2, X^4, X^6 into PRD slots 1..3 (PT) from X in slot 0, degree m
@@ -474,27 +489,30 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
     __syncwarp();
   }
   if (m != 13 || by_norm) return;
-  // d_p = ||X^p||^(1/p), p = 1..6, with X^3 = X^2 X and X^5 = X^4 X through T
-  double lg[7];
-  lg[1] = log2(nrm);
-  lg[2] = log2(norm1_smem<D>(A2, lane)) / 2.0;
-  lg[4] = log2(norm1_smem<D>(A4, lane)) / 4.0;
-  lg[6] = log2(norm1_smem<D>(A6, lane)) / 6.0;
+  // log2 d_p = log2 ||X^p|| / p, p = 1..6, with X^3 = X^2 X and X^5 = X^4 X
+  // through T.  Only the exponent of alpha matters, so the arithmetic is FP32
+  // (the estimate is inflated by 2^-12 to stay an upper bound).
+  float lg[7];
+  lg[1] = log2f(float(nrm));
+  lg[2] = log2_norm1_est<D>(A2, lane) * 0.5f;
+  lg[4] = log2_norm1_est<D>(A4, lane) * 0.25f;
+  lg[6] = log2_norm1_est<D>(A6, lane) * (1.0f / 6.0f);
   mm_slots<D, LD, LD>(A2, X, acc, sl);
   store_slots<D>(T, acc, sl);
   __syncwarp();
-  lg[3] = log2(norm1_smem<D>(T, lane)) / 3.0;
+  lg[3] = log2_norm1_est<D>(T, lane) * (1.0f / 3.0f);
   __syncwarp();
   mm_slots<D, LD, LD>(A4, X, acc, sl);
   __syncwarp();
   store_slots<D>(T, acc, sl);
   __syncwarp();
-  lg[5] = log2(norm1_smem<D>(T, lane)) / 5.0;
-  double la = lg[1];  // log2 alpha = min_p max(lg_p, lg_{p+1})
+  lg[5] = log2_norm1_est<D>(T, lane) * 0.2f;
+  float la = lg[1];  // log2 alpha = min_p max(lg_p, lg_{p+1})
 #pragma unroll
-  for (int p = 1; p <= 5; ++p) la = fmin(la, fmax(lg[p], lg[p + 1]));
-  const double lt = log2(THETA13);
-  int s0 = la > lt ? int(ceil(la - lt)) : 0;
+  for (int p = 1; p <= 5; ++p) la = fminf(la, fmaxf(lg[p], lg[p + 1]));
+  la += 1.0f / 4096.0f;
+  const float lt = 2.425436f;  // log2(theta_13) rounded down
+  int s0 = la > lt ? int(ceilf(la - lt)) : 0;
   // ell: ||(|X_s|)^27||_1 = max_j (1^T |X|^27)_j / 2^(27 s), by a normalised
   // row-vector iteration on |X| (FP32 is ample for an exponent estimate).
   __syncwarp();
@@ -504,7 +522,7 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
     float acc1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const float xkj = lane < D ? fabsf(float(X[k * LD + lane])) : 0.0f;
+      const float xkj = lane < D ? approx_abs_f32(X[k * LD + lane]) : 0.0f;
       acc1 = fmaf(__shfl_sync(FULL, v, k), xkj, acc1);
     }
     float mx = acc1;
@@ -515,8 +533,9 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
     v = acc1 / mx;
   }
   // ell = max(0, ceil(log2(|c27| ||(|X_s|)^27|| / ||X_s|| / u) / 26)), u = 2^-53
-  const double la27 = log2(pade13_c27()) + double(l27) - 27.0 * s0 - (lg[1] - s0);
-  int ell = int(ceil((la27 + 53.0) / 26.0));
+  constexpr float LOG2_C27 = -116.447f;  // log2((13!)^2 / (26! 27!))
+  const float la27 = LOG2_C27 + l27 - 27.0f * float(s0) - (lg[1] - float(s0));
+  int ell = int(ceilf((la27 + 53.0f) / 26.0f));
   if (!(ell > 0)) ell = 0;
   s = s0 + ell;
   if (s > 0) {
