@@ -158,11 +158,11 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
       continue;
     }
     const double ui = double(u[i]);
-    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n) : 0;
+    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, n, p.bc, k);
     const int r = int(i - st);
     const double a1 = p.c1 - p.fa * ui;
-    const int kr = recentring_shift(a1, p.dt, p.h, n, r);
+    const int kr = recentring_shift(a1, p.dt_h, n, r);
     const int hr = r - kr;
     // X (re-centred) and the two directions
     const double c1h = p.dt * a1 / p.h + double(kr);

@@ -82,6 +82,10 @@ KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int 
   p.c2 = op->c2;
   p.c3 = op->c3;
   p.fa = op->frozen_adv;
+  p.dt_h = dt / g->h;
+  p.c0dt = dt * op->c0;
+  p.c2h = dt * op->c2 / (g->h * g->h);
+  p.c3h = dt * op->c3 / (g->h * g->h * g->h);
   return p;
 }
 

@@ -125,11 +125,15 @@ __device__ __forceinline__ int64_t grid_index(int64_t q, int64_t N, int bc) {
   return q;
 }
 // Departure-centring shift clamp(floor(u dt / h + 1/2), -hs, hs), evaluated
-// with explicitly rounded FP64 operations so that the integer decision is
-// reproducible bit for bit.
-__device__ __forceinline__ int departure_shift(double u, double dt, double h, int n) {
+// with explicitly rounded FP64 operations, (u dt) / h + 1/2, so that the
+// integer decision is reproducible bit for bit.  dt_h = dt / h gives a cheap
+// estimate first; the exact division runs only when the estimate lies within
+// 1e-9 of an integer, where the two roundings could disagree.
+__device__ __forceinline__ int departure_shift(double u, double dt, double h, int n, double dt_h) {
   const int hs = (n - 1) >> 1;
-  const double t = __dadd_rn(__ddiv_rn(__dmul_rn(u, dt), h), 0.5);
+  double t = fma(u, dt_h, 0.5);
+  const double f = t - floor(t);
+  if (!(f > 1e-9 && f < 1.0 - 1e-9)) t = __dadd_rn(__ddiv_rn(__dmul_rn(u, dt), h), 0.5);
   // fmin/fmax return the non-NaN operand, so a non-finite state still gives a
   // window inside the clamp range (the non-finite result is flagged later).
   const double k = fmax(double(-hs), fmin(double(hs), floor(t)));
@@ -138,28 +142,30 @@ __device__ __forceinline__ int departure_shift(double u, double dt, double h, in
 // Exact integer re-centring of an exponential row: row r of exp(X(a)) equals
 // row r - k of exp(X(a) + k Dh1) (both evaluate e^{dt L} p at the same
 // departure point, Thm. 2).  k is the rounded local Courant number
-// -dt a1 / h, kept so that row r - k exists.
-__device__ __forceinline__ int recentring_shift(double a1, double dt, double h, int n, int r) {
-  const double cfl = __ddiv_rn(__dmul_rn(-dt, a1), h);
-  const double k = fmax(double(r - (n - 1)), fmin(double(r), floor(__dadd_rn(cfl, 0.5))));
+// -a1 dt / h, kept so that row r - k exists; any k in range gives the same
+// row, the rounded one the smallest matrix norm.
+__device__ __forceinline__ int recentring_shift(double a1, double dt_h, int n, int r) {
+  const double k = fmax(double(r - (n - 1)), fmin(double(r), floor(fma(-a1, dt_h, 0.5))));
   return int(k);
 }
 
 // ---------------------------------------------------------------- warp expm (a4)
-// Per-warp shared workspace layout (bytes):
-//   X64  double d x d (LD)         the (scaled-before-conversion) input
-//   PRD  5 x PT d x d (LD)         X, X^2, X^4, X^6 (or X^8), temporary
-//   G    double d x 2d (LDG)       [Q | P] -> [. | Q^-1 P]
-//   R1   double d x d (LD)         squaring ping-pong
-//   R2   double d x d (LD)         squaring ping-pong
-//   VEC  double 4 x 16             harvested rows
+// Per-warp shared workspace layout (bytes).  Buffers whose lifetimes do not
+// overlap share storage, which keeps the workspace small enough for 3 (FP64)
+// or 4 (FP32 form) CTAs of 4 warps per SM:
+//   X64 | R1   double d x d (LD)    input X; after the Pade products the
+//                                   solution R (or P in the one-row solve)
+//   PRD | G    5 x PT d x d (LD)    X, X^2, X^4, X^6, temporary; after the
+//                                   products the FP64 block [Q | P] (LDG)
+//   R2         double d x d (LD)    squaring ping-pong
+//   VEC        double 4 x 16        harvested rows
 template <typename PT>
 struct Ws {
   static constexpr int X64_OFF = 0;
   static constexpr int PRD_OFF = X64_OFF + DMAX * LD * 8;
-  static constexpr int G_OFF = PRD_OFF + 5 * DMAX * LD * int(sizeof(PT));
-  static constexpr int R1_OFF = G_OFF + DMAX * LDG * 8;
-  static constexpr int R2_OFF = R1_OFF + DMAX * LD * 8;
+  static constexpr int PRD_BYTES = 5 * DMAX * LD * int(sizeof(PT));
+  static constexpr int G_BYTES = DMAX * LDG * 8;
+  static constexpr int R2_OFF = PRD_OFF + (PRD_BYTES > G_BYTES ? PRD_BYTES : G_BYTES);
   static constexpr int VEC_OFF = R2_OFF + DMAX * LD * 8;
   static constexpr int BYTES = VEC_OFF + 4 * DMAX * 8;
   double* X64;
@@ -171,8 +177,8 @@ struct Ws {
   __device__ explicit Ws(unsigned char* base)
       : X64(reinterpret_cast<double*>(base + X64_OFF)),
         P(reinterpret_cast<PT*>(base + PRD_OFF)),
-        G(reinterpret_cast<double*>(base + G_OFF)),
-        R1(reinterpret_cast<double*>(base + R1_OFF)),
+        G(reinterpret_cast<double*>(base + PRD_OFF)),
+        R1(reinterpret_cast<double*>(base + X64_OFF)),
         R2(reinterpret_cast<double*>(base + R2_OFF)),
         V(reinterpret_cast<double*>(base + VEC_OFF)) {}
   __device__ PT* M(int q) const { return P + q * DMAX * LD; }
@@ -489,48 +495,76 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
     __syncwarp();
   }
   if (m != 13 || by_norm) return;
-  // log2 d_p = log2 ||X^p|| / p, p = 1..6, with X^3 = X^2 X and X^5 = X^4 X
-  // through T.  Only the exponent of alpha matters, so the arithmetic is FP32
-  // (the estimate is inflated by 2^-12 to stay an upper bound).
-  float lg[7];
-  lg[1] = log2f(float(nrm));
-  lg[2] = log2_norm1_est<D>(A2, lane) * 0.5f;
-  lg[4] = log2_norm1_est<D>(A4, lane) * 0.25f;
-  lg[6] = log2_norm1_est<D>(A6, lane) * (1.0f / 6.0f);
+  // log2 d_p = log2 ||X^p|| / p, p = 1..6, with X^3 = X^2 X (into T) and
+  // X^5 = X^4 X (into the R2 buffer, free at this point).  Only the exponent
+  // of alpha matters, so the arithmetic is FP32 (the estimate is inflated by
+  // 2^-12 to stay an upper bound); the six column-sum maxima are reduced
+  // together.
+  PT* A5 = reinterpret_cast<PT*>(w.R2);
   mm_slots<D, LD, LD>(A2, X, acc, sl);
   store_slots<D>(T, acc, sl);
-  __syncwarp();
-  lg[3] = log2_norm1_est<D>(T, lane) * (1.0f / 3.0f);
-  __syncwarp();
   mm_slots<D, LD, LD>(A4, X, acc, sl);
+  store_slots<D>(A5, acc, sl);
   __syncwarp();
-  store_slots<D>(T, acc, sl);
-  __syncwarp();
-  lg[5] = log2_norm1_est<D>(T, lane) * 0.2f;
+  float cs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (lane < D) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const int o = i * LD + lane;
+      cs[2] += approx_abs_f32(A2[o]);
+      cs[3] += approx_abs_f32(T[o]);
+      cs[4] += approx_abs_f32(A4[o]);
+      cs[5] += approx_abs_f32(A5[o]);
+      cs[6] += approx_abs_f32(A6[o]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+#pragma unroll
+    for (int p = 2; p <= 6; ++p) cs[p] = fmaxf(cs[p], __shfl_xor_sync(FULL, cs[p], o));
+  }
+  float lg[7];
+  lg[1] = log2f(float(nrm));
+#pragma unroll
+  for (int p = 2; p <= 6; ++p) lg[p] = log2f(cs[p]) / float(p);
   float la = lg[1];  // log2 alpha = min_p max(lg_p, lg_{p+1})
 #pragma unroll
   for (int p = 1; p <= 5; ++p) la = fminf(la, fmaxf(lg[p], lg[p + 1]));
   la += 1.0f / 4096.0f;
   const float lt = 2.425436f;  // log2(theta_13) rounded down
   int s0 = la > lt ? int(ceilf(la - lt)) : 0;
-  // ell: ||(|X_s|)^27||_1 = max_j (1^T |X|^27)_j / 2^(27 s), by a normalised
-  // row-vector iteration on |X| (FP32 is ample for an exponent estimate).
+  // ell: log2 ||(|X|)^27||_1 = log2 max_j (1^T |X|^27)_j by a row-vector
+  // iteration on |X| / ||X||_1 (entries then stay <= 13^4 between
+  // renormalisations every fourth step).  Lane j keeps column j of |X| in
+  // registers; the vector is broadcast through shared memory.
+  float* vs = reinterpret_cast<float*>(w.V);
+  const float inv_n = 1.0f / float(nrm);
+  float xc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) xc[k] = lane < D ? approx_abs_f32(X[k * LD + lane]) * inv_n : 0.0f;
+  if (lane < D) vs[lane] = 1.0f;
   __syncwarp();
-  float v = lane < D ? 1.0f : 0.0f;
-  float l27 = 0.0f;
-  for (int it = 0; it < 27; ++it) {
-    float acc1 = 0.0f;
+  float l27 = 27.0f * lg[1];
+  float vj = 0.0f;
+  for (int it = 1; it <= 27; ++it) {
+    float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const float xkj = lane < D ? approx_abs_f32(X[k * LD + lane]) : 0.0f;
-      acc1 = fmaf(__shfl_sync(FULL, v, k), xkj, acc1);
+    for (int k = 0; k < D; k += 2) {
+      a0 = fmaf(vs[k], xc[k], a0);
+      if (k + 1 < D) a1 = fmaf(vs[k + 1], xc[k + 1], a1);
     }
-    float mx = acc1;
+    vj = a0 + a1;
+    if ((it & 3) == 0 || it == 27) {
+      float mx = vj;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
-    if (!(mx > 0.0f)) { l27 = -1e30f; break; }
-    l27 += log2f(mx);
-    v = acc1 / mx;
+      for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+      if (!(mx > 0.0f)) { l27 = -1e30f; break; }
+      l27 += log2f(mx);
+      vj = vj / mx;
+    }
+    __syncwarp();
+    if (lane < D) vs[lane] = vj;
+    __syncwarp();
   }
   // ell = max(0, ceil(log2(|c27| ||(|X_s|)^27|| / ||X_s|| / u) / 26)), u = 2^-53
   constexpr float LOG2_C27 = -116.447f;  // log2((13!)^2 / (26! 27!))

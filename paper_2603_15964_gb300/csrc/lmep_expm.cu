@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_build_operator(KParams p, const 
   for (int64_t t = int64_t(blockIdx.x) * WARPS + (threadIdx.x >> 5); t < count; t += step) {
     const int64_t i = i0 + t;
     const double ui = u ? u[i] : 0.0;
-    const int k = (p.dep && u) ? departure_shift(ui, p.dt, p.h, p.n) : 0;
+    const int k = (p.dep && u) ? departure_shift(ui, p.dt, p.h, p.n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, p.n, p.bc, k);
     const int r = int(i - st);
     const double a1 = p.c1 - p.fa * ui;

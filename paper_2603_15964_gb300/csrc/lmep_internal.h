@@ -17,6 +17,8 @@ struct KParams {
   int n_phi;
   double bc_lo, bc_hi;
   double dt, c0, c1, c2, c3, fa;
+  // derived on the host once per launch: dt/h, dt c0, dt c2/h^2, dt c3/h^3
+  double dt_h, c0dt, c2h, c3h;
 };
 
 struct DeviceInfo {

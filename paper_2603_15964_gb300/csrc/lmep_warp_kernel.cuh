@@ -68,8 +68,13 @@ __device__ __forceinline__ void augment(double* X64, int n, int n_phi, int r, do
   }
 }
 
+// CTAs per SM the shared-memory workspace allows; the register budget is
+// capped to match so that registers do not limit occupancy further.
+template <typename PT>
+constexpr int ctas_per_sm() { return sizeof(PT) == 4 ? 4 : 3; }
+
 template <int D, typename PT>
-__global__ void __launch_bounds__(32 * WARPS) k_warp(WarpJob job) {
+__global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob job) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_warp(WarpJob job) {
       int nrows;
       double c1h = p.dt * p.c1 / h;
       if (p.n_phi == 0) {
-        const int kr = recentring_shift(p.c1, p.dt, h, n, r);
+        const int kr = recentring_shift(p.c1, p.dt / h, n, r);
         c1h += double(kr);
         rows[0] = r - kr;
         nrows = 1;
@@ -142,13 +147,12 @@ __global__ void __launch_bounds__(32 * WARPS) k_warp(WarpJob job) {
     // frozen velocity: point it
     const int64_t i = it;
     const double ui = double(u[i]);
-    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n) : 0;
+    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, n, p.bc, k);
     const int r = int(i - st);
     const double a1 = p.c1 - p.fa * ui;
-    const int kr = recentring_shift(a1, p.dt, p.h, n, r);
-    assemble<D>(w.X64, Dh, n, p.dt * p.c0, p.dt * a1 / p.h + double(kr), p.dt * p.c2 / (p.h * p.h),
-                p.dt * p.c3 / (p.h * p.h * p.h), lane);
+    const int kr = recentring_shift(a1, p.dt_h, n, r);
+    assemble<D>(w.X64, Dh, n, p.c0dt, fma(a1, p.dt_h, double(kr)), p.c2h, p.c3h, lane);
     __syncwarp();
     const int hr = r - kr;
     int m_, s_, a_;
