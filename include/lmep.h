@@ -188,6 +188,30 @@ LMEP_API lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const
                               double* dnu_dev, void* scratch_dev, size_t scratch_bytes,
                               int32_t precision, void* stream);
 
+/* The same reverse step as lmep_adjoint_step, for callers that cannot
+ * allocate device memory: a plug-in whose host application's allocator owns
+ * the whole device, a latency-critical loop that must not enter the driver's
+ * allocator, a sandbox with a device budget fixed before the library loads.
+ * This entry point allocates nothing and takes no handle: its scratch is a
+ * file-scope static __device__ array of 8 MiB inside the library, held by
+ * every GPU that loads the library until the process exits.  The paper has
+ * no counterpart; this is an interface for such callers only.
+ *  - Limit: grids needing more than 8 MiB of scratch (N (n + 1) elements of
+ *    the state dtype + 4 N + 256 bytes, e.g. N <= 61680 at n = 15 in FP64)
+ *    are rejected with LMEP_ERR_INVALID and a message; use lmep_adjoint_step.
+ *  - The first call on each device, with that device current, looks up the
+ *    array's device address (cudaGetSymbolAddress) and caches it; make that
+ *    first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents;
+ *    every scratch element a call reads is written earlier in the same call.
+ *    Calls that overlap on the GPU (other streams, other threads) race on it.
+ *  - Non-finite results are not reported by this entry point (there is no
+ *    handle); check the outputs.
+ * Arguments and dnu_dev accumulation are those of lmep_adjoint_step. */
+LMEP_API lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_operator* op, double dt,
+                                               const void* u_dev, const void* lam_next_dev, void* lam_dev,
+                                               double* dnu_dev, int32_t precision, void* stream);
+
 /* Diagnostics of the frozen-velocity path: for every point i write
  * stats_dev[3 i .. 3 i + 2] = (Pade degree m, squarings s, full squarings a)
  * exactly as the fused step chooses them for state u_dev (the remaining

@@ -21,7 +21,7 @@ from ._lib import BC, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
 
 __all__ = ["Grid", "Operator", "Handle", "lmep_build_operator", "lmep_expm", "lmep_harvest_weights",
            "lmep_step", "lmep_batch_workspace_bytes", "lmep_batch_prepare", "lmep_step_batched",
-           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_frozen_stats", "lmep_sync_status", "lmep_fma_peak",
+           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_sync_status", "lmep_fma_peak",
            "state_dtype", "LmepError"]
 
 
@@ -162,6 +162,13 @@ def lmep_adjoint_step(h: Handle, grid: Grid, op: Operator, dt: float, u, lam_nex
     _lib.call("lmep_adjoint_step", h.ptr, C.byref(grid.c()), C.byref(op.c()), dt, _ptr(u), _ptr(lam_next),
               _ptr(lam), _ptr(dnu), _ptr(scratch), scratch.numel() * scratch.element_size(), PREC[precision],
               _stream(stream))
+
+
+def lmep_adjoint_step_noalloc(grid: Grid, op: Operator, dt: float, u, lam_next, lam, dnu,
+                              precision: str = "fp64", stream=None) -> None:
+    """lmep_adjoint_step without caller scratch or handle (library-static scratch, no allocation)."""
+    _lib.call("lmep_adjoint_step_noalloc", C.byref(grid.c()), C.byref(op.c()), dt, _ptr(u), _ptr(lam_next),
+              _ptr(lam), _ptr(dnu), PREC[precision], _stream(stream))
 
 
 def lmep_frozen_stats(h: Handle, grid: Grid, op: Operator, dt: float, u, stats, precision: str = "fp64",

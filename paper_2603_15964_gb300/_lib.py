@@ -62,6 +62,8 @@ _SIGS = {
     "lmep_adjoint_scratch_bytes": [C.POINTER(LmepGrid), C.c_int32, C.POINTER(C.c_size_t)],
     "lmep_adjoint_step": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, _P, _P, _P,
                           C.c_size_t, C.c_int32, _P],
+    "lmep_adjoint_step_noalloc": [C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, _P, _P,
+                                  C.c_int32, _P],
     "lmep_frozen_stats": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, C.c_int32, _P],
     "lmep_sync_status": [_P, _P],
     "lmep_fma_peak": [C.c_int32, C.POINTER(C.c_double)],

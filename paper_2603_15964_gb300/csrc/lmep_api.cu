@@ -97,6 +97,10 @@ int default_tile(bool mixed) { return mixed ? 2048 : 1024; }
 
 }  // namespace
 
+namespace lmep {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace lmep
+
 extern "C" {
 
 const char* lmep_version(void) { return "lmep-gb300 0.1 (sm_103a)"; }

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace lmep {
@@ -20,6 +21,9 @@ struct KParams {
   // derived on the host once per launch: dt/h, dt c0, dt c2/h^2, dt c3/h^3
   double dt_h, c0dt, c2h, c3h;
 };
+
+// Set the thread-local text returned by lmep_last_error().
+void set_last_error(const std::string& msg);
 
 struct DeviceInfo {
   int sms;
