@@ -169,17 +169,27 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ GPU leg
 def flops_model(n: int, stats, fp32_form: bool):
-    """Algorithmic FLOPs of one point-update given (m, s, a): (FP32 part, FP64 part)."""
+    """Algorithmic FLOPs of one point-update given (m, s, a): (FP32 part, FP64 part).
+
+    Pade products: pi_m matrix products of 2 d^3 (Higham 2005, Table 2.2).
+    s = 0 (one harvested row): one row of q_m^-1 p_m = an LU-equivalent solve
+    (2/3) d^3 + 2 d^2 plus y^T P (2 d^2; FP32 in the FP32 form).
+    s > 0: the full solve (8/3) d^3, a full squarings of 2 d^3 and
+    2^(s-a) - 1 row products of 2 d^2.  Apply: 2 d.  The kernel's own extra
+    work (norms of powers for the scaling choice) is not counted.
+    """
     import numpy as np
     m, s, a = stats[:, 0], stats[:, 1], stats[:, 2]
     d = float(n)
     prod = np.vectorize(lambda mm: PI_M.get(int(mm), 6))(m) * 2 * d ** 3
-    solve = (8.0 / 3.0) * d ** 3
+    one_row = s == 0
+    solve = np.where(one_row, (2.0 / 3.0) * d ** 3 + 2 * d * d, (8.0 / 3.0) * d ** 3)
+    ytp = np.where(one_row, 2 * d * d, 0.0)
     sq = a * 2 * d ** 3 + ((2.0 ** (s - a)) - 1) * 2 * d * d
     apply_ = 2 * d
     if fp32_form:
-        return float(np.sum(prod + apply_)), float(np.sum(solve + sq))
-    return 0.0, float(np.sum(prod + apply_ + solve + sq))
+        return float(np.sum(prod + apply_ + ytp)), float(np.sum(solve + sq))
+    return 0.0, float(np.sum(prod + apply_ + ytp + solve + sq))
 
 
 def gpu_leg(args, rank: int, world: int, local_rank: int):
@@ -339,6 +349,161 @@ def stated_error(results, tasks, res):
     return out
 
 
+# ------------------------------------------------------------------ Allen-Cahn batch (HBM-bound apply)
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (profiling recipe, 6.8 TB/s)"
+
+
+def _oracle_ac(task):
+    """Worker: one oracle ETDRK2 step of one Allen-Cahn instance."""
+    B, b, seed = task
+    import workloads as wl
+    from oracle import lmep as olmep
+    batch = wl.allen_cahn_batch(B=B, seed=seed, steps=1)
+    p = batch.problem(b)
+    return olmep.run(p, wl.allen_cahn_ic(p.N, b), 1)
+
+
+def allen_cahn_main(args, rank, world, local_rank, cores):
+    import numpy as np
+
+    import workloads as wl
+    B = args.instances
+    pool = None
+    if rank == 0 and world == 1:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(cores)
+        pool.map(_oracle_points, [(7, 1.0, 0, [1])] * cores)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        batch = wl.allen_cahn_batch(B=B, seed=0, steps=1)
+        small = [b for b in np.argsort(batch.Ns)[: max(cores, 4)]]
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_ac, [(B, int(b), 0) for b in small])
+        dt = time.perf_counter() - t0
+        pts = float(sum(int(batch.Ns[b]) for b in small)) * args.steps
+        pool.close()
+        v = pts / dt
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": allen_cahn_config(B, batch),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": f"one ETDRK2 step of the {len(small)} smallest instances per step"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    from paper_2603_15964_gb300.batch import BatchedProblem, LaunchShape, autotune
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    batch = wl.allen_cahn_batch(B=B, seed=rank, steps=args.steps)
+    hs = [batch.problem(b).h for b in range(B)]
+    op = L.Operator(c2=batch.eps2)
+    from paper_2603_15964_gb300.batch import pack
+    u0s = [wl.allen_cahn_ic(int(batch.Ns[b]), b) for b in range(B)]
+    cands = [LaunchShape(t, bl, c) for t in (2048, 4096, 8192) for bl in (256, 512) for c in (0, 2)]
+    shape, timings = autotune(batch.Ns, hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",
+                              candidates=cands, use_cache=False)
+    prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",
+                          shape)
+    u = pack(u0s, torch.float32)            # instances 16-byte aligned (library layout)
+    work = torch.empty_like(u)
+    first = u.clone()
+    tmp = torch.empty_like(u)
+    L.lmep_step_batched_once(prob.handle, prob.workspace, first, tmp)
+    first = tmp.cpu().numpy()
+    prob.capture(u, work)
+    prob.replay(max(args.warmup, 3) * 2)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    prob.replay(args.steps)
+    b.record()
+    b.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    L.lmep_sync_status(prob.handle)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    pts = prob.points * args.steps * world
+    # e2e: host state in, one step, host state out (pinned), through the public API
+    hin = u.detach().cpu().pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    e2e_n = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e2e_n):
+        u.copy_(hin, non_blocking=True)
+        L.lmep_step_batched_once(prob.handle, prob.workspace, u, work)
+        hout.copy_(work, non_blocking=True)
+    e1.record()
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    peak, peak_src = measured_hbm_peak()
+    per_launch_ms = ms / args.steps
+    bytes_launch = 8.0 * prob.points
+    achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    cpu = err = None
+    if pool is not None:
+        small = [int(b) for b in np.argsort(batch.Ns)[: max(cores, 4)]]
+        t0 = time.perf_counter()
+        outs = pool.map(_oracle_ac, [(B, b, rank) for b in small])
+        dt = time.perf_counter() - t0
+        pool.close()
+        npts = sum(int(batch.Ns[b]) for b in small)
+        cpu = {"value": npts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one ETDRK2 step of the {len(small)} smallest instances ({npts} point-updates)"}
+        worst = 0.0
+        for b, want in zip(small, outs):
+            got = first[prob.offsets[b]:prob.offsets[b] + int(batch.Ns[b])]
+            worst = max(worst, float(np.max(np.abs(got - want)) / max(np.max(np.abs(want)), 1e-300)))
+        err = {"fp32": worst}
+    line = {"metric": METRIC, "value": pts / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": allen_cahn_config(B, batch),
+            "error": {"vs": "FP64 oracle, one step, smallest instances", "rel_linf": err},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_apply<float, ETDRK2, Allen-Cahn> (one persistent launch per step)",
+                         "algorithmic_bytes_per_launch": bytes_launch},
+            "autotune": {"chosen": shape.__dict__, "ms_per_step": timings},
+            "cpu_baseline": cpu,
+            "e2e": {"value": prob.points * e2e_n / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * prob.total, "d2h_bytes_per_step": 4 * prob.total},
+            "gpu_launches": args.steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def allen_cahn_config(B, batch):
+    return {"workload": f"batched Allen-Cahn u_t = 1e-4 u_xx + u - u^3 on [-1,1], {B} instances, N log-uniform "
+                        "in [1024, 65536], periodic or Neumann (Bernoulli 1/2), n = 9, ETDRK2, dt = 0.5 h_min^2/1e-4, "
+                        "one persistent CUDA-graph launch per step, FP32 state and accumulation",
+            "points_per_step": int(sum(int(v) for v in batch.Ns)),
+            "l2": "state (254 MB FP32) larger than L2; no flush"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -346,6 +511,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle points per instance (cpu_baseline)")
+    ap.add_argument("--workload", choices=["burgers", "allen_cahn"], default="burgers",
+                    help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply")
+    ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -353,6 +521,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     cores = os.cpu_count() or 1
+    if args.workload == "allen_cahn":
+        return allen_cahn_main(args, rank, world, local_rank, cores)
 
     if args.impl == "reference":
         if rank != 0:

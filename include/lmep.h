@@ -71,14 +71,18 @@ typedef enum { LMEP_N_NONE = 0, LMEP_N_ALLEN_CAHN = 1, LMEP_N_KDV = 2 } lmep_non
  *         wall node.  Periodic: centred window, indices mod N.
  *  n      stencil width, odd, 3 <= n <= 15, n <= N.
  *  departure_centring  frozen-velocity problems only: shift each window
- *         upstream by k_i = clamp(floor(u_i dt / h + 1/2), -(n-1)/2, (n-1)/2). */
+ *         upstream by k_i = clamp(floor(u_i dt / h + 1/2), -(n-1)/2, (n-1)/2).
+ *  batch  number of independent instances of this grid stored back to back
+ *         (state arrays hold batch * N values; 0 means 1).  Honoured by the
+ *         frozen-velocity step and harvest, lmep_frozen_stats and
+ *         lmep_adjoint_step; the other calls require batch <= 1. */
 typedef struct lmep_grid {
   int64_t N;
   double h;
   int32_t bc;
   int32_t n;
   int32_t departure_centring;
-  int32_t reserved0;
+  int32_t batch;
   double bc_lo, bc_hi;
 } lmep_grid;
 
@@ -122,7 +126,7 @@ LMEP_API lmep_status lmep_expm(lmep_handle* h, const double* A_dev, int64_t P, i
  *  u_frozen_dev == NULL: constant coefficients; W_dev receives [n][1+n_phi][n]:
  *      W[r][k][:] = row r of dt^k phi_k(dt L) (k = 0: exp(dt L)) for every row class r.
  *  u_frozen_dev != NULL: frozen velocity (requires n_phi == 0): W_dev receives
- *      [N][1][n], the weights of point i on its own window (zeros at Dirichlet walls).
+ *      [batch][N][1][n], the weights of point i on its own window (zeros at Dirichlet walls).
  *      u_frozen_dev has the state dtype of `precision`.
  * W dtype: double for LMEP_PREC_FP64, float for LMEP_PREC_MIXED. */
 LMEP_API lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_operator* op,
@@ -138,8 +142,9 @@ LMEP_API lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, co
  *      first-derivative matrix on the same window.
  *  W_dev == NULL: frozen velocity: every point rebuilds and exponentiates its
  *      own operator every step ((a1)-(a6) fused); requires the linear scheme.
- *  u_dev, work_dev: state dtype of `precision`, N elements each; work_dev is
- *  scratch of the same size; the result is left in u_dev. */
+ *  u_dev, work_dev: state dtype of `precision`, N elements each (batch * N for
+ *  the frozen-velocity step); work_dev is scratch of the same size; the result
+ *  is left in u_dev. */
 LMEP_API lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, int32_t scheme,
                       int32_t nonlin, double dt, const void* W_dev, void* u_dev, void* work_dev,
                       int64_t nsteps, int32_t precision, void* stream);
@@ -149,8 +154,11 @@ LMEP_API lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_op
  * dt, the operator and precision; each has its own N_b, h_b and bc_b (periodic
  * or Neumann).  The caller allocates a workspace of lmep_batch_workspace_bytes
  * bytes; lmep_batch_prepare fills it (tile table and per-instance weights,
- * harvested on the device) and must run before lmep_step_batched.  State u is
- * the concatenation of all instances (offsets = exclusive prefix sum of N_b). */
+ * harvested on the device) and must run before lmep_step_batched.  State u
+ * holds the instances back to back, instance b starting at element
+ * o_b = sum_{c<b} round_up(N_c, 4) (every instance 16-byte aligned); the up to
+ * three padding elements after an instance are never read or written.  The
+ * state arrays therefore hold o_B = sum_b round_up(N_b, 4) elements. */
 typedef struct lmep_batch_desc {
   int64_t B;                 /* number of instances */
   const int64_t* N_host;     /* [B] points per instance */
@@ -172,6 +180,12 @@ LMEP_API lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d
                                size_t workspace_bytes, int32_t precision, void* stream);
 LMEP_API lmep_status lmep_step_batched(lmep_handle* h, const void* workspace_dev, void* u_dev,
                               void* work_dev, int64_t nsteps, void* stream);
+
+/* One step of a prepared batch from u_in_dev to u_out_dev (distinct buffers,
+ * no copy): one persistent launch, suitable for replay in a CUDA graph that
+ * alternates the two buffers. */
+LMEP_API lmep_status lmep_step_batched_once(lmep_handle* h, const void* workspace_dev, const void* u_in_dev,
+                                            void* u_out_dev, void* stream);
 
 /* (a7) one reverse step of the frozen-velocity linear scheme (Dirichlet or
  * periodic), given the forward state u^n:
@@ -207,6 +221,7 @@ LMEP_API lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const
  *    Calls that overlap on the GPU (other streams, other threads) race on it.
  *  - Non-finite results are not reported by this entry point (there is no
  *    handle); check the outputs.
+ *  - One instance per call: grids with batch > 1 are rejected.
  * Arguments and dnu_dev accumulation are those of lmep_adjoint_step. */
 LMEP_API lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_operator* op, double dt,
                                                const void* u_dev, const void* lam_next_dev, void* lam_dev,

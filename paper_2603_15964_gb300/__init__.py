@@ -21,6 +21,7 @@ from ._lib import BC, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
 
 __all__ = ["Grid", "Operator", "Handle", "lmep_build_operator", "lmep_expm", "lmep_harvest_weights",
            "lmep_step", "lmep_batch_workspace_bytes", "lmep_batch_prepare", "lmep_step_batched",
+           "lmep_step_batched_once",
            "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_sync_status", "lmep_fma_peak",
            "state_dtype", "LmepError"]
 
@@ -36,9 +37,10 @@ class Grid:
     departure_centring: bool = False
     bc_lo: float = 0.0
     bc_hi: float = 0.0
+    batch: int = 1
 
     def c(self) -> _lib.LmepGrid:
-        return _lib.LmepGrid(self.N, self.h, BC[self.bc], self.n, int(self.departure_centring), 0,
+        return _lib.LmepGrid(self.N, self.h, BC[self.bc], self.n, int(self.departure_centring), self.batch,
                              self.bc_lo, self.bc_hi)
 
 
@@ -149,6 +151,10 @@ def lmep_batch_prepare(h: Handle, Ns, hs, bcs, n, scheme, nonlin, dt, op: Operat
 
 def lmep_step_batched(h: Handle, workspace, u, work, nsteps: int, stream=None) -> None:
     _lib.call("lmep_step_batched", h.ptr, _ptr(workspace), _ptr(u), _ptr(work), nsteps, _stream(stream))
+
+
+def lmep_step_batched_once(h: Handle, workspace, u_in, u_out, stream=None) -> None:
+    _lib.call("lmep_step_batched_once", h.ptr, _ptr(workspace), _ptr(u_in), _ptr(u_out), _stream(stream))
 
 
 def lmep_adjoint_scratch_bytes(grid: Grid, precision: str = "fp64") -> int:

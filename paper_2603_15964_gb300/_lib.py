@@ -23,7 +23,7 @@ NONLIN = {"none": 0, "allen_cahn": 1, "kdv": 2}
 
 class LmepGrid(C.Structure):
     _fields_ = [("N", C.c_int64), ("h", C.c_double), ("bc", C.c_int32), ("n", C.c_int32),
-                ("departure_centring", C.c_int32), ("reserved0", C.c_int32),
+                ("departure_centring", C.c_int32), ("batch", C.c_int32),
                 ("bc_lo", C.c_double), ("bc_hi", C.c_double)]
 
 
@@ -59,6 +59,7 @@ _SIGS = {
     "lmep_batch_workspace_bytes": [C.POINTER(LmepBatchDesc), C.c_int32, C.POINTER(C.c_size_t)],
     "lmep_batch_prepare": [_P, C.POINTER(LmepBatchDesc), _P, C.c_size_t, C.c_int32, _P],
     "lmep_step_batched": [_P, _P, _P, _P, C.c_int64, _P],
+    "lmep_step_batched_once": [_P, _P, _P, _P, _P],
     "lmep_adjoint_scratch_bytes": [C.POINTER(LmepGrid), C.c_int32, C.POINTER(C.c_size_t)],
     "lmep_adjoint_step": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, _P, _P, _P,
                           C.c_size_t, C.c_int32, _P],

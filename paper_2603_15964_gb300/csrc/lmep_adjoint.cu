@@ -148,16 +148,20 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
                    b5 = pade_b(13, 5), b4 = pade_b(13, 4), b3 = pade_b(13, 3), b2 = pade_b(13, 2),
                    b1 = pade_b(13, 1), b0 = pade_b(13, 0);
   double dnu_acc = 0.0;
-  for (int64_t i = int64_t(blockIdx.x) * AW + warp; i < p.N; i += int64_t(gridDim.x) * AW) {
+  const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
+  for (int64_t it = int64_t(blockIdx.x) * AW + warp; it < items; it += int64_t(gridDim.x) * AW) {
+    const int64_t bb = it / p.N;
+    const int64_t i = it - bb * p.N;
+    const ST* ub = u + bb * p.N;
     if (dir && (i == 0 || i == p.N - 1)) {
-      for (int j = lane; j < n; j += 32) Wout[i * n + j] = ST(0);
+      for (int j = lane; j < n; j += 32) Wout[it * n + j] = ST(0);
       if (lane == 0) {
-        gu_out[i] = ST(0);
-        st_out[i] = 0;
+        gu_out[it] = ST(0);
+        st_out[it] = 0;
       }
       continue;
     }
-    const double ui = double(u[i]);
+    const double ui = double(ub[i]);
     const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, n, p.bc, k);
     const int r = int(i - st);
@@ -268,14 +272,14 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     }
     // outputs: w = R[hr], g_q = L_q[hr] . u[window]
     double uj = 0.0;
-    if (lane < n) uj = double(u[grid_index(st + lane, p.N, p.bc)]);
+    if (lane < n) uj = double(ub[grid_index(st + lane, p.N, p.bc)]);
     const double gu = warp_sum(lane < n ? LU[0][hr * LD + lane] * uj : 0.0);
     const double gn = warp_sum(lane < n ? LU[1][hr * LD + lane] * uj : 0.0);
-    if (lane < n) Wout[i * n + lane] = ST(R[hr * LD + lane]);
+    if (lane < n) Wout[it * n + lane] = ST(R[hr * LD + lane]);
     if (lane == 0) {
-      gu_out[i] = ST(gu);
-      st_out[i] = int32_t(st - i);
-      dnu_acc += double(lam_next[i]) * gn;
+      gu_out[it] = ST(gu);
+      st_out[it] = int32_t(st - i);
+      dnu_acc += double(lam_next[it]) * gn;
     }
     __syncwarp();
   }
@@ -292,7 +296,10 @@ __global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, con
   const int n = p.n;
   const bool dir = p.bc == BC_DIRICHLET;
   unsigned bad = 0;
-  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < p.N; k += int64_t(gridDim.x) * blockDim.x) {
+  const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
+  for (int64_t kg = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; kg < items; kg += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t base = (kg / p.N) * p.N;  // first point of this instance
+    const int64_t k = kg - base;
     ST acc = ST(0);
     for (int d = -(n - 1); d <= n - 1; ++d) {
       int64_t i = k + d;
@@ -301,13 +308,13 @@ __global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, con
       } else {
         i = grid_index(i, p.N, BC_PERIODIC);
       }
-      const int64_t sti = i + st_rel[i];
+      const int64_t sti = i + st_rel[base + i];
       int64_t j = k - sti;
       if (!dir) j = grid_index(j, p.N, BC_PERIODIC);
-      if (j >= 0 && j < n) acc = fma(lam_next[i], W[i * n + j], acc);
+      if (j >= 0 && j < n) acc = fma(lam_next[base + i], W[(base + i) * n + j], acc);
     }
-    if (!dir || (k >= 1 && k <= p.N - 2)) acc = fma(lam_next[k], gu[k], acc);
-    lam[k] = acc;
+    if (!dir || (k >= 1 && k <= p.N - 2)) acc = fma(lam_next[kg], gu[kg], acc);
+    lam[kg] = acc;
     bad |= !isfinite(double(acc));
   }
   if (bad) atomicOr(flags, 1u);
@@ -316,9 +323,10 @@ __global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, con
 template <int D, typename ST>
 cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
                         void* scratch, unsigned* flags, cudaStream_t s) {
+  const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
   ST* W = static_cast<ST*>(scratch);
-  ST* gu = W + p.N * p.n;
-  int32_t* st = reinterpret_cast<int32_t*>(gu + p.N);
+  ST* gu = W + items * p.n;
+  int32_t* st = reinterpret_cast<int32_t*>(gu + items);
   const size_t smem = DHB + AW * WSB;
   auto k1 = k_adjoint_points<D, ST>;
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -327,14 +335,14 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32 * AW, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = int64_t(device_info().sms) * per_sm;
-  const int64_t need = (p.N + AW - 1) / AW;
+  const int64_t need = (items + AW - 1) / AW;
   if (need < grid) grid = need;
   k1<<<int(grid), 32 * AW, smem, s>>>(p, static_cast<const ST*>(u), static_cast<const ST*>(lam_next), W, gu, st,
                                       dnu);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int blk = 256;
-  int64_t g2 = (p.N + blk - 1) / blk;
+  int64_t g2 = (items + blk - 1) / blk;
   if (g2 > int64_t(device_info().sms) * 16) g2 = int64_t(device_info().sms) * 16;
   k_adjoint_gather<ST><<<int(g2), blk, 0, s>>>(p, static_cast<const ST*>(lam_next), W, gu, st, static_cast<ST*>(lam),
                                               flags);

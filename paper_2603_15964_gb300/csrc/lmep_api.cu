@@ -55,6 +55,8 @@ lmep_status check_grid(const lmep_grid* g, int n_phi) {
   if (g->N > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "N too large");
   if (!(g->h > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
   if (g->bc < 0 || g->bc > 2) return fail(LMEP_ERR_INVALID, "unknown boundary condition");
+  if (g->batch < 0) return fail(LMEP_ERR_INVALID, "batch must be >= 0");
+  if (g->N * (g->batch > 1 ? g->batch : 1) > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "batch * N too large");
   if (n_phi < 0 || n_phi > 2) return fail(LMEP_ERR_INVALID, "n_phi must be 0, 1 or 2");
   if (g->n + n_phi > 16) return fail(LMEP_ERR_UNSUPPORTED, "n + n_phi must be <= 16");
   return LMEP_OK;
@@ -69,6 +71,7 @@ lmep_status check_prec(int32_t precision) {
 KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int n_phi) {
   KParams p{};
   p.N = g->N;
+  p.batch = g->batch > 1 ? g->batch : 1;
   p.h = g->h;
   p.bc = g->bc;
   p.n = g->n;
@@ -152,6 +155,7 @@ lmep_status lmep_build_operator(lmep_handle* h, const lmep_grid* g, const lmep_o
   if (!h || !op) return fail(LMEP_ERR_INVALID, "handle/operator is NULL");
   lmep_status st = check_grid(g, n_phi);
   if (st != LMEP_OK) return st;
+  if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "lmep_build_operator takes batch <= 1");
   if (count < 0 || i0 < 0 || i0 + count > g->N) return fail(LMEP_ERR_INVALID, "point range outside grid");
   if (count == 0) return LMEP_OK;
   if (!M_dev || !start_dev || !row_dev) return fail(LMEP_ERR_INVALID, "output pointer is NULL");
@@ -193,6 +197,7 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
     return LMEP_OK;
   }
   if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "frozen operator needs u_frozen_dev");
+  if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "constant-coefficient harvest takes batch <= 1");
   CK(lmep::launch_harvest_const(p, nullptr, 1, W_dev, mixed, S(stream)), "harvest(constant)");
   return LMEP_OK;
 }
@@ -228,11 +233,15 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     }
   } else {
     if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
+    if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "stored-weight stepping takes batch <= 1 (use lmep_batch_*)");
     if (nonlin == 2 && g->bc != LMEP_BC_PERIODIC) return fail(LMEP_ERR_UNSUPPORTED, "KdV needs a periodic grid");
-    const int H = lmep::apply_halo(g->n, scheme, nonlin, g->bc);
-    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 2) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
+    const bool fast = nonlin != 2 && g->bc != LMEP_BC_DIRICHLET;
+    const int H = fast ? lmep::apply_fast_halo(g->n, scheme) : lmep::apply_halo(g->n, scheme, nonlin, g->bc);
+    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
+    if (g->bc == LMEP_BC_PERIODIC && g->N < H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
     ApplyParams a{};
     a.halo = H;
+    a.fast = fast ? 1 : 0;
     a.n = g->n;
     a.scheme = scheme;
     a.nonlin = nonlin;
@@ -256,7 +265,8 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
       std::swap(cur, nxt);
     }
   }
-  if (cur != u_dev) CK(cudaMemcpyAsync(u_dev, cur, size_t(g->N) * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
+  const size_t total = size_t(g->N) * size_t(W_dev ? 1 : (g->batch > 1 ? g->batch : 1));
+  if (cur != u_dev) CK(cudaMemcpyAsync(u_dev, cur, total * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
   return LMEP_OK;
 }
 
@@ -281,13 +291,13 @@ lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayou
   if (tile % 256 != 0 || tile > 16384) return fail(LMEP_ERR_INVALID, "tile must be a multiple of 256, <= 16384");
   if (d->block != 0 && d->block != 128 && d->block != 256 && d->block != 512)
     return fail(LMEP_ERR_INVALID, "block must be 128, 256 or 512");
-  const int H = lmep::apply_halo(d->n, d->scheme, d->nonlin, LMEP_BC_PERIODIC);
+  const int H = lmep::apply_fast_halo(d->n, d->scheme);
   int64_t ntiles = 0;
   for (int64_t b = 0; b < d->B; ++b) {
     const int64_t N = d->N_host[b];
     if (d->bc_host[b] != LMEP_BC_PERIODIC && d->bc_host[b] != LMEP_BC_NEUMANN)
       return fail(LMEP_ERR_INVALID, "batch instances must be periodic or Neumann");
-    if (N < 2 * H + 2 || N < d->n) return fail(LMEP_ERR_UNSUPPORTED, "instance too small for the halo");
+    if (N < 2 * H + 8 || N < d->n) return fail(LMEP_ERR_UNSUPPORTED, "instance too small for the halo");
     if (!(d->h_host[b] > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
     ntiles += (N + tile - 1) / tile;
   }
@@ -333,7 +343,7 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
     inst[b].bc = d->bc_host[b];
     inst[b].pad = 0;
     for (int64_t t0 = 0; t0 < inst[b].N; t0 += L.tile) tiles.push_back(make_int2(int(b), int(t0)));
-    off += inst[b].N;
+    off += (inst[b].N + 3) / 4 * 4;  // every instance starts on a 16-byte boundary
   }
   char* base = static_cast<char*>(ws);
   CK(cudaMemcpyAsync(base + L.inst_off, inst.data(), inst.size() * sizeof(Instance), cudaMemcpyHostToDevice,
@@ -358,7 +368,8 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
   a.n = d->n;
   a.scheme = d->scheme;
   a.nonlin = d->nonlin;
-  a.halo = lmep::apply_halo(d->n, d->scheme, d->nonlin, LMEP_BC_PERIODIC);
+  a.halo = lmep::apply_fast_halo(d->n, d->scheme);
+  a.fast = 1;
   a.tile = L.tile;
   a.dt = d->dt;
   a.inst = reinterpret_cast<const Instance*>(base + L.inst_off);
@@ -400,13 +411,26 @@ lmep_status lmep_step_batched(lmep_handle* h, const void* ws, void* u_dev, void*
   return LMEP_OK;
 }
 
+lmep_status lmep_step_batched_once(lmep_handle* h, const void* ws, const void* u_in_dev, void* u_out_dev,
+                                   void* stream) {
+  if (!h || !ws || !u_in_dev || !u_out_dev) return fail(LMEP_ERR_INVALID, "NULL argument");
+  if (u_in_dev == u_out_dev) return fail(LMEP_ERR_INVALID, "u_in_dev and u_out_dev must differ");
+  auto it = h->plans.find(ws);
+  if (it == h->plans.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
+  const BatchPlan& plan = it->second;
+  CK(lmep::launch_apply(plan.ap, u_in_dev, u_out_dev, plan.W, plan.mixed, plan.block, plan.grid, h->flags,
+                        S(stream)),
+     "step_batched_once");
+  return LMEP_OK;
+}
+
 lmep_status lmep_adjoint_scratch_bytes(const lmep_grid* g, int32_t precision, size_t* bytes_out) {
   if (!bytes_out) return fail(LMEP_ERR_INVALID, "bytes_out is NULL");
   lmep_status st = check_grid(g, 0);
   if (st != LMEP_OK) return st;
   st = check_prec(precision);
   if (st != LMEP_OK) return st;
-  *bytes_out = lmep::adjoint_scratch_bytes(g->N, g->n, precision == LMEP_PREC_MIXED);
+  *bytes_out = lmep::adjoint_scratch_bytes(g->N * (g->batch > 1 ? g->batch : 1), g->n, precision == LMEP_PREC_MIXED);
   return LMEP_OK;
 }
 
@@ -423,7 +447,8 @@ lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_ope
   if (!u_dev || !lam_next_dev || !lam_dev || !dnu_dev || !scratch_dev) return fail(LMEP_ERR_INVALID, "NULL buffer");
   if (lam_dev == lam_next_dev) return fail(LMEP_ERR_INVALID, "lam_dev must differ from lam_next_dev");
   const bool mixed = precision == LMEP_PREC_MIXED;
-  if (scratch_bytes < lmep::adjoint_scratch_bytes(g->N, g->n, mixed)) return fail(LMEP_ERR_NOMEM, "scratch too small");
+  if (scratch_bytes < lmep::adjoint_scratch_bytes(g->N * (g->batch > 1 ? g->batch : 1), g->n, mixed))
+    return fail(LMEP_ERR_NOMEM, "scratch too small");
   CK(lmep::launch_adjoint(make_params(g, op, dt, 0), u_dev, lam_next_dev, lam_dev, dnu_dev, scratch_dev, mixed,
                           h->flags, S(stream)), "adjoint");
   return LMEP_OK;

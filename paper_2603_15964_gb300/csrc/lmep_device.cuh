@@ -163,7 +163,8 @@ template <typename PT>
 struct Ws {
   static constexpr int X64_OFF = 0;
   static constexpr int PRD_OFF = X64_OFF + DMAX * LD * 8;
-  static constexpr int PRD_BYTES = 5 * DMAX * LD * int(sizeof(PT));
+  static constexpr int LDM = sizeof(PT) == 4 ? 20 : LD;   // row stride of the PT matrices
+  static constexpr int PRD_BYTES = 5 * DMAX * LDM * int(sizeof(PT));
   static constexpr int G_BYTES = DMAX * LDG * 8;
   static constexpr int R2_OFF = PRD_OFF + (PRD_BYTES > G_BYTES ? PRD_BYTES : G_BYTES);
   static constexpr int VEC_OFF = R2_OFF + DMAX * LD * 8;
@@ -181,7 +182,7 @@ struct Ws {
         R1(reinterpret_cast<double*>(base + X64_OFF)),
         R2(reinterpret_cast<double*>(base + R2_OFF)),
         V(reinterpret_cast<double*>(base + VEC_OFF)) {}
-  __device__ PT* M(int q) const { return P + q * DMAX * LD; }
+  __device__ PT* M(int q) const { return P + q * DMAX * LDM; }
 };
 
 // Element slots of a d x d matrix spread over a warp: lane owns e = lane + 32 t.
@@ -223,39 +224,128 @@ __device__ __forceinline__ void store_slots(T* __restrict__ C, const T (&v)[Slot
     if (sl.ok[t]) C[sl.i[t] * LD + sl.j[t]] = v[t];
 }
 
-// v = c0*M0 + c1*M1 + c2*M2 (+ cI on the diagonal), per slot, read from shared memory.
+// Per-lane output positions of a D x D product in the Pade phase.
+//  * double: the element slots above (lane owns e = lane + 32 t), row stride 17;
+//    FP64 products are bound by the FP64 pipe, so padding would only add work.
+//  * float: register blocks.  The matrix is padded to DP x DP (DP = 8 or 16);
+//    lane l owns rows {rq, rq + DP/RB, ..} (rq = l / 4) and the CB consecutive
+//    columns from cq * CB (cq = l % 4).  Per k it loads RB row-broadcast
+//    scalars of A and one CB-wide vector of B (row stride 20 floats keeps the
+//    vectors 16-byte aligned and the 8 broadcast rows on distinct banks), so a
+//    product costs ~4x fewer shared-memory wavefronts than the slot layout.
+template <int D, typename PT>
+struct Lay;
+
+template <int D>
+struct Lay<D, double> {
+  static constexpr int N = Slots<D>::S;
+  static constexpr int LDM = LD;
+  int i[N], j[N];
+  bool ok[N];
+  __device__ explicit Lay(int lane) {
+    const Slots<D> sl(lane);
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+      i[t] = sl.i[t];
+      j[t] = sl.j[t];
+      ok[t] = sl.ok[t];
+    }
+  }
+  __device__ __forceinline__ void mm(const double* __restrict__ A, const double* __restrict__ B,
+                                     double (&acc)[N]) const {
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc[t] = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+      for (int t = 0; t < N; ++t) acc[t] = fma(A[i[t] * LDM + k], B[k * LDM + j[t]], acc[t]);
+    }
+  }
+};
+
+template <int D>
+struct Lay<D, float> {
+  static constexpr int DP = D <= 8 ? 8 : 16;
+  static constexpr int RB = DP == 8 ? 1 : 2;
+  static constexpr int CB = DP == 8 ? 2 : 4;
+  static constexpr int RS = DP / RB;  // row stride between a lane's rows (= 8)
+  static constexpr int N = RB * CB;
+  static constexpr int LDM = 20;
+  int rq, cq;
+  int i[N], j[N];
+  bool ok[N];
+  __device__ explicit Lay(int lane) : rq(lane >> 2), cq(lane & 3) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) {
+      i[t] = rq + RS * (t / CB);
+      j[t] = cq * CB + (t % CB);
+      ok[t] = i[t] < D && j[t] < D;
+    }
+  }
+  __device__ __forceinline__ void mm(const float* __restrict__ A, const float* __restrict__ B,
+                                     float (&acc)[N]) const {
+#pragma unroll
+    for (int t = 0; t < N; ++t) acc[t] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      float a[RB], b[CB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) a[r] = A[(rq + RS * r) * LDM + k];
+      if constexpr (CB == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(B + k * LDM + cq * 4);
+        b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(B + k * LDM + cq * 2);
+        b[0] = v.x; b[1] = v.y;
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r * CB + c] = fmaf(a[r], b[c], acc[r * CB + c]);
+    }
+  }
+};
+
 template <int D, typename T>
-__device__ __forceinline__ void lincomb(T (&v)[Slots<D>::S], const Slots<D>& sl, const T* M0, T c0,
+__device__ __forceinline__ void lay_store(const Lay<D, T>& L, T* __restrict__ C, const T (&v)[Lay<D, T>::N]) {
+#pragma unroll
+  for (int t = 0; t < Lay<D, T>::N; ++t)
+    if (L.ok[t]) C[L.i[t] * Lay<D, T>::LDM + L.j[t]] = v[t];
+}
+
+// v = c0*M0 + c1*M1 + c2*M2 (+ cI on the diagonal) at the lane's positions (add: v += ...).
+template <int D, typename T>
+__device__ __forceinline__ void lincomb(const Lay<D, T>& L, T (&v)[Lay<D, T>::N], const T* M0, T c0,
                                         const T* M1, T c1, const T* M2, T c2, T cI, bool add) {
 #pragma unroll
-  for (int t = 0; t < Slots<D>::S; ++t) {
-    const int o = sl.i[t] * LD + sl.j[t];
+  for (int t = 0; t < Lay<D, T>::N; ++t) {
+    const int o = L.i[t] * Lay<D, T>::LDM + L.j[t];
     T x = add ? v[t] : T(0);
     if (M0) x = fma(c0, M0[o], x);
     if (M1) x = fma(c1, M1[o], x);
     if (M2) x = fma(c2, M2[o], x);
-    if (sl.i[t] == sl.j[t]) x += cI;
+    if (L.i[t] == L.j[t]) x += cI;
     v[t] = x;
   }
 }
 
-// Odd part U and even part V of p_m(X) for the lane's slots; X is PRD slot 0
-// and X^2, X^4, X^6 (as far as m needs them) are in slots 1..3.  Products
+// Odd part U and even part V of p_m(X) at the lane's positions; X is PRD slot
+// 0 and X^2, X^4, X^6 (as far as m needs them) are in slots 1..3.  Products
 // follow Higham (2005) eqs. (2.10)-(2.11); the degree only changes which
 // powers exist and which coefficients multiply them, so every degree shares
-// the same product call sites.  Uses PRD slot 4 as scratch.
+// the same product call sites.  Uses PRD slot 4 and the R2 buffer as scratch.
 template <int D, typename PT>
-__device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& sl, PT (&U)[Slots<D>::S],
-                                        PT (&V)[Slots<D>::S]) {
-  constexpr int S = Slots<D>::S;
+__device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Lay<D, PT>& L, PT (&U)[Lay<D, PT>::N],
+                                        PT (&V)[Lay<D, PT>::N]) {
+  constexpr int N = Lay<D, PT>::N;
   PT* X = w.M(0);
   PT* A2 = w.M(1);
   PT* A4 = w.M(2);
   PT* A6 = w.M(3);
   PT* T = w.M(4);
-  PT acc[S], A8[S];
+  PT* T2 = reinterpret_cast<PT*>(w.R2);
+  PT acc[N], A8[N];
   PT b[14];
-  (void)A4;
 #pragma unroll
   for (int j = 0; j < 14; ++j) b[j] = PT(0);
   switch (m) {
@@ -279,56 +369,66 @@ __device__ __forceinline__ void pade_uv(const Ws<PT>& w, int m, const Slots<D>& 
 #pragma unroll
       for (int j = 0; j <= 13; ++j) b[j] = PT(pade_b(13, j));
   }
-  // X^2, X^4, X^6 are already in PRD slots 1..3 (see powers_and_scaling);
-  // X^8 for m = 9 in registers
-  if (m == 9) mm_slots<D, LD, LD>(A6, A2, A8, sl);
-  const PT* P2 = A2;
-  const PT* P4 = m >= 5 ? A4 : nullptr;
-  const PT* P6 = m >= 7 ? A6 : nullptr;
   if (m == 13) {
     // U-inner = A6 (b13 A6 + b11 A4 + b9 A2) + b7 A6 + b5 A4 + b3 A2 + b1 I
     // V       = A6 (b12 A6 + b10 A4 + b8 A2) + b6 A6 + b4 A4 + b2 A2 + b0 I
-#pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-      const int o = pass == 0 ? 1 : 0;  // odd (U-inner) or even (V) coefficients
-      lincomb<D>(acc, sl, A6, b[12 + o], A4, b[10 + o], A2, b[8 + o], PT(0), false);
-      __syncwarp();
-      store_slots<D>(T, acc, sl);
-      __syncwarp();
-      mm_slots<D, LD, LD>(A6, T, acc, sl);
-      lincomb<D>(acc, sl, A6, b[6 + o], A4, b[4 + o], A2, b[2 + o], b[o], true);
-      if (pass == 0) {
-#pragma unroll
-        for (int t = 0; t < S; ++t) U[t] = acc[t];
-      } else {
-#pragma unroll
-        for (int t = 0; t < S; ++t) V[t] = acc[t];
-      }
-    }
-    // U-inner goes back to T for the final product
+    lincomb<D>(L, acc, A6, b[13], A4, b[11], A2, b[9], PT(0), false);
+    lay_store<D>(L, T, acc);
+    lincomb<D>(L, acc, A6, b[12], A4, b[10], A2, b[8], PT(0), false);
+    lay_store<D>(L, T2, acc);
     __syncwarp();
-    store_slots<D>(T, U, sl);
+    L.mm(A6, T, acc);
+    lincomb<D>(L, acc, A6, b[7], A4, b[5], A2, b[3], b[1], true);
+    L.mm(A6, T2, V);
+    lincomb<D>(L, V, A6, b[6], A4, b[4], A2, b[2], b[0], true);
+    __syncwarp();
+    lay_store<D>(L, T, acc);  // U-inner for the last product
   } else {
-    lincomb<D>(acc, sl, P6, b[7], P4, b[5], P2, b[3], b[1], false);
-    lincomb<D>(V, sl, P6, b[6], P4, b[4], P2, b[2], b[0], false);
+    const PT* P2 = A2;
+    const PT* P4 = m >= 5 ? A4 : nullptr;
+    const PT* P6 = m >= 7 ? A6 : nullptr;
+    if (m == 9) L.mm(A6, A2, A8);
+    lincomb<D>(L, acc, P6, b[7], P4, b[5], P2, b[3], b[1], false);
+    lincomb<D>(L, V, P6, b[6], P4, b[4], P2, b[2], b[0], false);
     if (m == 9) {
 #pragma unroll
-      for (int t = 0; t < S; ++t) {
+      for (int t = 0; t < N; ++t) {
         acc[t] = fma(b[9], A8[t], acc[t]);
         V[t] = fma(b[8], A8[t], V[t]);
       }
     }
-    store_slots<D>(T, acc, sl);
+    lay_store<D>(L, T, acc);
   }
   __syncwarp();
-  mm_slots<D, LD, LD>(X, T, U, sl);
+  L.mm(X, T, U);
   __syncwarp();
+}
+
+// 1/x by Newton-Raphson for the reciprocal, r <- r + r (1 - x r), from an FP32
+// seed (__frcp_rn of x rounded to 20 mantissa bits, relative error < 2^-19):
+// each step squares the relative error, so two steps reach the FP64 rounding
+// level; one step (relative error < 2^-38) is used for the FP32 form, whose
+// inputs carry FP32 rounding errors five orders of magnitude larger.  The float <-> double conversions act on the bit patterns (exact for
+// the seed), so only the four Newton FMAs use the FP64 pipe.  Outside the
+// normal float range the correctly rounded __drcp_rn is used instead.
+template <int STEPS>
+__device__ __forceinline__ double recip_nr(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 1 || e >= 253) return __drcp_rn(x);
+  const float xf = __int_as_float((hi & int(0x80000000)) | (e << 23) | ((hi & 0xfffff) << 3));
+  const int rb = __float_as_int(__frcp_rn(xf));
+  const int re = ((rb >> 23) & 0xff) - 127 + 1023;
+  double r = __hiloint2double((rb & int(0x80000000)) | (re << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+#pragma unroll
+  for (int it = 0; it < STEPS; ++it) r = fma(r, fma(-x, r, 1.0), r);
+  return r;
 }
 
 // Solve Q R = P in place on G = [Q | P] by Gauss-Jordan elimination with
 // partial pivoting (FP64).  On return G[:, D:2D] holds R.  Pivot magnitudes
 // are compared as IEEE bit patterns (monotonic for non-negative doubles).
-template <int D>
+template <int D, int NEWTON = 2>
 __device__ void gauss_jordan(double* G, int lane, int ncols = 2 * D) {
   for (int k = 0; k < D; ++k) {
     long long key = -1;
@@ -354,7 +454,7 @@ __device__ void gauss_jordan(double* G, int lane, int ncols = 2 * D) {
       }
     }
     __syncwarp();
-    const double inv = __drcp_rn(G[k * LDG + k]);
+    const double inv = recip_nr<NEWTON>(G[k * LDG + k]);
     for (int j = k + 1 + lane; j < ncols; j += 32) G[k * LDG + j] *= inv;
     __syncwarp();
     const int nc = ncols - k - 1;
@@ -427,19 +527,6 @@ __device__ __forceinline__ float approx_abs_f32(double x) {
 }
 __device__ __forceinline__ float approx_abs_f32(float x) { return fabsf(x); }
 
-// log2 of the 1-norm (max column sum) of a D x D matrix, FP32 estimate, all lanes.
-template <int D, typename T>
-__device__ __forceinline__ float log2_norm1_est(const T* M, int lane) {
-  float cs = 0.0f;
-  if (lane < D) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) cs += approx_abs_f32(M[i * LD + lane]);
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(FULL, cs, o));
-  return log2f(cs);
-}
-
 // 1-norm (max column sum) of a D x D matrix in shared memory, all lanes.
 template <int D, typename T>
 __device__ __forceinline__ double norm1_smem(const T* M, int lane) {
@@ -455,8 +542,9 @@ __device__ __forceinline__ double norm1_smem(const T* M, int lane) {
 // and scaling s.  m = 13 uses the Al-Mohy & Higham (2009) choice of s (see the
 // file header); the powers are then scaled by exact powers of two.
 template <int D, typename PT>
-__device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane, double nrm, int& m, int& s) {
-  constexpr int S = Slots<D>::S;
+__device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lane, double nrm, int& m, int& s) {
+  constexpr int S = Lay<D, PT>::N;
+  constexpr int LM = Lay<D, PT>::LDM;
   PT* X = w.M(0);
   PT* A2 = w.M(1);
   PT* A4 = w.M(2);
@@ -478,20 +566,20 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
     const PT sc = PT(ldexp(1.0, -s));
 #pragma unroll
     for (int q = 0; q < S; ++q)
-      if (sl.ok[q]) X[sl.i[q] * LD + sl.j[q]] *= sc;
+      if (L.ok[q]) X[L.i[q] * LM + L.j[q]] *= sc;
     __syncwarp();
   }
-  mm_slots<D, LD, LD>(X, X, acc, sl);
-  store_slots<D>(A2, acc, sl);
+  L.mm(X, X, acc);
+  lay_store<D>(L, A2, acc);
   __syncwarp();
   if (m >= 5) {
-    mm_slots<D, LD, LD>(A2, A2, acc, sl);
-    store_slots<D>(A4, acc, sl);
+    L.mm(A2, A2, acc);
+    lay_store<D>(L, A4, acc);
     __syncwarp();
   }
   if (m >= 7) {
-    mm_slots<D, LD, LD>(A4, A2, acc, sl);
-    store_slots<D>(A6, acc, sl);
+    L.mm(A4, A2, acc);
+    lay_store<D>(L, A6, acc);
     __syncwarp();
   }
   if (m != 13 || by_norm) return;
@@ -501,16 +589,16 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
   // 2^-12 to stay an upper bound); the six column-sum maxima are reduced
   // together.
   PT* A5 = reinterpret_cast<PT*>(w.R2);
-  mm_slots<D, LD, LD>(A2, X, acc, sl);
-  store_slots<D>(T, acc, sl);
-  mm_slots<D, LD, LD>(A4, X, acc, sl);
-  store_slots<D>(A5, acc, sl);
+  L.mm(A2, X, acc);
+  lay_store<D>(L, T, acc);
+  L.mm(A4, X, acc);
+  lay_store<D>(L, A5, acc);
   __syncwarp();
   float cs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   if (lane < D) {
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const int o = i * LD + lane;
+      const int o = i * LM + lane;
       cs[2] += approx_abs_f32(A2[o]);
       cs[3] += approx_abs_f32(T[o]);
       cs[4] += approx_abs_f32(A4[o]);
@@ -533,35 +621,53 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
   la += 1.0f / 4096.0f;
   const float lt = 2.425436f;  // log2(theta_13) rounded down
   int s0 = la > lt ? int(ceilf(la - lt)) : 0;
-  // ell: log2 ||(|X|)^27||_1 = log2 max_j (1^T |X|^27)_j by a row-vector
-  // iteration on |X| / ||X||_1 (entries then stay <= 13^4 between
-  // renormalisations every fourth step).  Lane j keeps column j of |X| in
-  // registers; the vector is broadcast through shared memory.
-  float* vs = reinterpret_cast<float*>(w.V);
-  const float inv_n = 1.0f / float(nrm);
-  float xc[D];
+  // ell: log2 ||(|X|)^27||_1 = log2 max_j (1^T |X|^27)_j.  With Y = |X| / ||X||_1
+  // (so that nothing overflows), 1^T Y^27 = ((1^T (Y^4)^6) Y^2) Y: two FP32
+  // products (Y^2, Y^4 of a nonnegative matrix, no cancellation) and eight
+  // renormalised row-vector steps.  Lane j keeps column j of the current
+  // matrix in registers; the vector is broadcast through shared memory.
+  __syncwarp();
+  // Always FP32 (an exponent estimate), in the FP32 register-block layout, in
+  // buffers that are free at this point (X^3, X^5 and the double input).
+  const Lay<D, float> LF(lane);
+  constexpr int LMF = Lay<D, float>::LDM;
+  constexpr int NF = Lay<D, float>::N;
+  float* Y = reinterpret_cast<float*>(T);
+  float* Y2 = reinterpret_cast<float*>(A5);
+  float* Y4 = reinterpret_cast<float*>(w.R1);
+  {
+    const float sc = float(1.0 / nrm);
 #pragma unroll
-  for (int k = 0; k < D; ++k) xc[k] = lane < D ? approx_abs_f32(X[k * LD + lane]) * inv_n : 0.0f;
+    for (int q = 0; q < NF; ++q)
+      if (LF.ok[q]) Y[LF.i[q] * LMF + LF.j[q]] = approx_abs_f32(X[LF.i[q] * LM + LF.j[q]]) * sc;
+  }
+  __syncwarp();
+  float accf[NF];
+  LF.mm(Y, Y, accf);
+  lay_store<D>(LF, Y2, accf);
+  __syncwarp();
+  LF.mm(Y2, Y2, accf);
+  lay_store<D>(LF, Y4, accf);
+  __syncwarp();
+  float* vs = reinterpret_cast<float*>(w.V);
   if (lane < D) vs[lane] = 1.0f;
   __syncwarp();
   float l27 = 27.0f * lg[1];
-  float vj = 0.0f;
-  for (int it = 1; it <= 27; ++it) {
+  for (int it = 0; it < 8; ++it) {
+    const float* M = it < 6 ? Y4 : (it == 6 ? Y2 : Y);
     float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
     for (int k = 0; k < D; k += 2) {
-      a0 = fmaf(vs[k], xc[k], a0);
-      if (k + 1 < D) a1 = fmaf(vs[k + 1], xc[k + 1], a1);
+      a0 = fmaf(vs[k], lane < D ? M[k * LMF + lane] : 0.0f, a0);
+      if (k + 1 < D) a1 = fmaf(vs[k + 1], lane < D ? M[(k + 1) * LMF + lane] : 0.0f, a1);
     }
-    vj = a0 + a1;
-    if ((it & 3) == 0 || it == 27) {
-      float mx = vj;
+    float vj = a0 + a1;
+    float mx = vj;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
-      if (!(mx > 0.0f)) { l27 = -1e30f; break; }
-      l27 += log2f(mx);
-      vj = vj / mx;
-    }
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+    if (!(mx > 0.0f)) { l27 = -1e30f; break; }
+    l27 += log2f(mx);
+    vj = vj / mx;
     __syncwarp();
     if (lane < D) vs[lane] = vj;
     __syncwarp();
@@ -577,8 +683,8 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Slots<D>& sl, int lane
              c6 = PT(ldexp(1.0, -6 * s));
 #pragma unroll
     for (int q = 0; q < S; ++q) {
-      if (sl.ok[q]) {
-        const int o = sl.i[q] * LD + sl.j[q];
+      if (L.ok[q]) {
+        const int o = L.i[q] * LM + L.j[q];
         X[o] *= c1;
         A2[o] *= c2;
         A4[o] *= c4;
@@ -597,43 +703,93 @@ template <int D, typename PT>
 __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
                                        double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr) {
   constexpr int S = Slots<D>::S;
+  constexpr int NL = Lay<D, PT>::N;
+  constexpr int LM = Lay<D, PT>::LDM;
   const Slots<D> sl(lane);
-  const double nrm = norm1_smem<D>(w.X64, lane);
+  const Lay<D, PT> L(lane);
+  constexpr bool F32 = sizeof(PT) == 4;
+  // ||X||_1 picks the Pade degree.  The FP32 form estimates it in FP32 and
+  // falls back to the FP64 sum only next to a threshold, where the estimate
+  // (relative error < 2^-16) could pick another degree.
+  double nrm;
+  if (F32) {
+    float cs = 0.0f;
+    if (lane < D) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) cs += approx_abs_f32(w.X64[i * LD + lane]);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(FULL, cs, o));
+    nrm = double(cs);
+    const double th[6] = {THETA3, THETA5, THETA7, THETA9, THETA13, 8192.0};
+    bool near = !(cs > 0.0f) || !(cs < 3.0e38f);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) near |= fabs(nrm - th[q]) <= 1e-4 * th[q];
+    if (near) nrm = norm1_smem<D>(w.X64, lane);
+  } else {
+    nrm = norm1_smem<D>(w.X64, lane);
+  }
   PT* X = w.M(0);
 #pragma unroll
-  for (int t = 0; t < S; ++t)
-    if (sl.ok[t]) X[sl.i[t] * LD + sl.j[t]] = PT(w.X64[sl.i[t] * LD + sl.j[t]]);
+  for (int t = 0; t < NL; ++t)
+    if (L.ok[t]) X[L.i[t] * LM + L.j[t]] = PT(w.X64[L.i[t] * LD + L.j[t]]);
   __syncwarp();
   int m, s;
-  powers_and_scaling<D, PT>(w, sl, lane, nrm, m, s);
-  PT U[S], V[S];
-  pade_uv<D, PT>(w, m, sl, U, V);
+  powers_and_scaling<D, PT>(w, L, lane, nrm, m, s);
+  PT U[NL], V[NL];
+  pade_uv<D, PT>(w, m, L, U, V);
   int a = s;
   if (!full && s == 0 && nrows == 1) {
-    // one row of Q^-1 P: y^T Q = e_r^T (Gauss-Jordan on [Q^T | e_r]), w = y^T P
+    // one row of Q^-1 P: y^T Q = e_r^T (Gauss-Jordan on [Q^T | e_r]), w = y^T P.
+    // Q = V - U is formed exactly in FP64.  In the FP32 form the numerator
+    // P = V + U and the product y^T P stay FP32 (FP32 accumulation).
+    PT* Pm = reinterpret_cast<PT*>(w.R1);
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-      if (sl.ok[t]) {
+    for (int t = 0; t < NL; ++t) {
+      if (L.ok[t]) {
         const double u = double(U[t]), v = double(V[t]);
-        w.G[sl.j[t] * LDG + sl.i[t]] = v - u;
-        w.R1[sl.i[t] * LD + sl.j[t]] = v + u;
+        w.G[L.j[t] * LDG + L.i[t]] = v - u;
+        if (F32) Pm[L.i[t] * LM + L.j[t]] = V[t] + U[t];
+        else w.R1[L.i[t] * LD + L.j[t]] = v + u;
       }
     }
     if (lane < D) w.G[lane * LDG + D] = lane == rows[0] ? 1.0 : 0.0;
     __syncwarp();
-    gauss_jordan<D>(w.G, lane, D + 1);
-    if (lane < D) w.V[lane] = w.G[lane * LDG + D];
-    __syncwarp();
-    rows_times<D>(w.V, w.R1, LD, 1, lane);
+    gauss_jordan<D, F32 ? 1 : 2>(w.G, lane, D + 1);
+    if (F32) {
+      float* ys = reinterpret_cast<float*>(w.V) + 2 * DMAX;
+      if (lane < D) ys[lane] = float(w.G[lane * LDG + D]);
+      __syncwarp();
+      constexpr int K0 = (D + 1) / 2;
+      const int j = lane & 15, half = lane >> 4;
+      float acc = 0.0f;
+      if (j < D) {
+        if (half == 0) {
+#pragma unroll
+          for (int k = 0; k < K0; ++k) acc = fmaf(ys[k], float(Pm[k * LM + j]), acc);
+        } else {
+#pragma unroll
+          for (int k = K0; k < D; ++k) acc = fmaf(ys[k], float(Pm[k * LM + j]), acc);
+        }
+      }
+      acc += __shfl_xor_sync(FULL, acc, 16);
+      __syncwarp();
+      if (half == 0 && j < D) w.V[j] = double(acc);
+      __syncwarp();
+    } else {
+      if (lane < D) w.V[lane] = w.G[lane * LDG + D];
+      __syncwarp();
+      rows_times<D>(w.V, w.R1, LD, 1, lane);
+    }
     a = 0;
   } else {
     // [Q | P] = [V - U | V + U] in FP64
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-      if (sl.ok[t]) {
+    for (int t = 0; t < NL; ++t) {
+      if (L.ok[t]) {
         const double u = double(U[t]), v = double(V[t]);
-        w.G[sl.i[t] * LDG + sl.j[t]] = v - u;
-        w.G[sl.i[t] * LDG + D + sl.j[t]] = v + u;
+        w.G[L.i[t] * LDG + L.j[t]] = v - u;
+        w.G[L.i[t] * LDG + D + L.j[t]] = v + u;
       }
     }
     __syncwarp();

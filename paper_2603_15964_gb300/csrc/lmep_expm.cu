@@ -139,7 +139,7 @@ cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused
   WarpJob job{};
   job.mode = fused ? MODE_FROZEN_STEP : MODE_FROZEN_W;
   job.p = p;
-  job.items = p.N;
+  job.items = p.N * (p.batch > 1 ? p.batch : 1);
   job.u = u;
   job.out = out;
   job.flags = flags;

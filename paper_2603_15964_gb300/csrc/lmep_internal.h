@@ -11,6 +11,7 @@ namespace lmep {
 // Problem parameters passed by value to every kernel.
 struct KParams {
   int64_t N;
+  int64_t batch;  // instances of N points stored back to back (0 or 1: one)
   double h;
   int bc;
   int n;
@@ -52,7 +53,8 @@ struct Instance {
 };
 struct ApplyParams {
   int n, scheme, nonlin, tile;
-  int halo;          // staged halo per side (apply_halo)
+  int halo;          // staged halo per side (apply_halo / apply_fast_halo)
+  int fast;          // 1: register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
   double dt;
   double bc_lo, bc_hi;
   // instance table (device) and tile table (device, int2 = {instance, start})
@@ -67,6 +69,7 @@ struct ApplyParams {
   int bc;
 };
 int apply_halo(int n, int scheme, int nonlin, int bc);
+int apply_fast_halo(int n, int scheme);
 size_t apply_smem_bytes(int tile, int halo, int scheme, bool mixed);
 cudaError_t launch_apply(const ApplyParams& a, const void* u, void* out, const void* W, bool mixed,
                          int block, int grid, unsigned* flags, cudaStream_t s);

@@ -68,8 +68,9 @@ __device__ __forceinline__ void augment(double* X64, int n, int n_phi, int r, do
   }
 }
 
-// CTAs per SM the shared-memory workspace allows; the register budget is
-// capped to match so that registers do not limit occupancy further.
+// CTAs per SM: the FP32 form fits 4 CTAs of 4 warps in shared memory and in
+// 128 registers per thread; the FP64 path fits 3 (measured faster than 2 CTAs
+// with the full register file, despite some spills at n = 13).
 template <typename PT>
 constexpr int ctas_per_sm() { return sizeof(PT) == 4 ? 4 : 3; }
 
@@ -88,22 +89,8 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
   const ST* u = static_cast<const ST*>(job.u);
   ST* out = static_cast<ST*>(job.out);
   const bool dir = p.bc == BC_DIRICHLET;
-  const bool frozen = mode == MODE_FROZEN_W || mode == MODE_FROZEN_STEP;
-  if (frozen && dir && out && blockIdx.x == 0 && warp == 0) {
-    if (mode == MODE_FROZEN_STEP) {
-      if (lane == 0) out[0] = ST(p.bc_lo);
-      if (lane == 1) out[p.N - 1] = ST(p.bc_hi);
-    } else {
-      for (int j = lane; j < n; j += 32) {
-        out[j] = ST(0);
-        out[(p.N - 1) * n + j] = ST(0);
-      }
-    }
-  }
-  const int64_t first = (frozen && dir) ? 1 : 0;
-  const int64_t last = (frozen && dir) ? job.items - 1 : job.items;
   unsigned bad = 0;
-  for (int64_t it = first + int64_t(blockIdx.x) * WARPS + warp; it < last; it += int64_t(gridDim.x) * WARPS) {
+  for (int64_t it = int64_t(blockIdx.x) * WARPS + warp; it < job.items; it += int64_t(gridDim.x) * WARPS) {
     if (mode == MODE_FULL) {
       for (int e = lane; e < D * D; e += 32) w.X64[(e / D) * LD + e % D] = job.A[it * D * D + e];
       __syncwarp();
@@ -144,9 +131,21 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       __syncwarp();
       continue;
     }
-    // frozen velocity: point it
-    const int64_t i = it;
-    const double ui = double(u[i]);
+    // frozen velocity: point i of instance b (instances of N points back to back)
+    const int64_t b = it / p.N;
+    const int64_t i = it - b * p.N;
+    const ST* ub = u + b * p.N;
+    if (dir && (i == 0 || i == p.N - 1)) {  // walls keep their values; no weights
+      if (out) {
+        if (mode == MODE_FROZEN_STEP) {
+          if (lane == 0) out[it] = ST(i == 0 ? p.bc_lo : p.bc_hi);
+        } else {
+          for (int j = lane; j < n; j += 32) out[it * n + j] = ST(0);
+        }
+      }
+      continue;
+    }
+    const double ui = double(ub[i]);
     const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, n, p.bc, k);
     const int r = int(i - st);
@@ -155,12 +154,15 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
     assemble<D>(w.X64, Dh, n, p.c0dt, fma(a1, p.dt_h, double(kr)), p.c2h, p.c3h, lane);
     __syncwarp();
     const int hr = r - kr;
+    // the window values are loaded now so that their latency hides behind the expm
+    ST uw = ST(0);
+    if (mode == MODE_FROZEN_STEP && lane < n) uw = ub[grid_index(st + lane, p.N, p.bc)];
     int m_, s_, a_;
     warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, &m_, &s_, &a_);
     if (job.ms && lane == 0) {
-      job.ms[3 * i] = m_;
-      job.ms[3 * i + 1] = s_;
-      job.ms[3 * i + 2] = a_;
+      job.ms[3 * it] = m_;
+      job.ms[3 * it + 1] = s_;
+      job.ms[3 * it + 2] = a_;
     }
     if (!out) {
       __syncwarp();
@@ -168,14 +170,14 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
     }
     if (mode == MODE_FROZEN_STEP) {
       ST acc = ST(0);
-      if (lane < n) acc = ST(w.V[lane]) * u[grid_index(st + lane, p.N, p.bc)];
+      if (lane < n) acc = ST(w.V[lane]) * uw;
       acc = warp_sum(acc);
       if (lane == 0) {
-        out[i] = acc;
+        out[it] = acc;
         bad |= !isfinite(double(acc));
       }
     } else {
-      if (lane < n) out[i * n + lane] = ST(w.V[lane]);
+      if (lane < n) out[it * n + lane] = ST(w.V[lane]);
     }
     __syncwarp();
   }

@@ -1,0 +1,103 @@
+"""Adjoint through torch.autograd with step checkpointing (frozen-velocity Burgers).
+
+J = (h/2) sum_b ||u_b(T) - u*_b||^2.  The gradient with respect to the
+initial states and nu is checked against the FP64 oracle's reverse sweep
+(oracle.adjoint.gradient, one instance at a time), against central
+differences of the GPU forward pass, and for independence of the checkpoint
+interval.  Tolerances: FP64 path 1e-9 relative (a gradient through T steps of
+Frechet derivatives), FP32 form 1e-4.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import adjoint as oadj
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2603_15964_gb300 as L
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return L
+
+
+def problem(steps=7):
+    return wl.burgers(N=64, n=7, cfl=1.5, nu=3e-4, steps=steps, departure_centring=True)
+
+
+def solver_for(p, precision, K):
+    from paper_2603_15964_gb300.autograd import FrozenVelocitySolver
+    return FrozenVelocitySolver(N=p.N, h=p.h, n=p.n, dt=p.dt, steps=p.steps, precision=precision,
+                                checkpoint_every=K)
+
+
+def loss_and_grads(L, p, precision, K, u0, target):
+    dt_ = L.state_dtype(precision)
+    x = torch.tensor(u0, dtype=dt_, device="cuda", requires_grad=True)
+    nu = torch.tensor(p.c2, dtype=torch.float64, requires_grad=True)
+    uT = solver_for(p, precision, K)(x, nu)
+    J = 0.5 * p.h * ((uT.double() - torch.tensor(target, device="cuda")) ** 2).sum()
+    J.backward()
+    return float(J), x.grad.double().cpu().numpy(), float(nu.grad)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gradient_matches_oracle(L, precision):
+    p = problem()
+    B = 2
+    u0 = np.stack([wl.burgers_ic(p.N, 3 + b) for b in range(B)])
+    target = np.stack([wl.burgers_ic(p.N, 1003 + b) for b in range(B)])
+    if precision == "mixed":
+        u0 = u0.astype(np.float32).astype(np.float64)
+    J, gu, gnu = loss_and_grads(L, p, precision, 3, u0, target)
+    want_J, want_nu = 0.0, 0.0
+    want_u = np.zeros_like(u0)
+    for b in range(B):
+        Jb, gb, nb = oadj.gradient(p, u0[b], target[b], p.steps)
+        want_J += Jb
+        want_u[b] = gb
+        want_nu += nb
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert abs(J - want_J) <= tol * abs(want_J) + (0 if precision == "fp64" else 1e-6)
+    assert np.max(np.abs(gu - want_u)) <= tol * np.max(np.abs(want_u))
+    assert abs(gnu - want_nu) <= tol * abs(want_nu)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(L):
+    p = problem(steps=9)
+    u0 = np.stack([wl.burgers_ic(p.N, 8)])
+    target = np.stack([wl.burgers_ic(p.N, 1008)])
+    a = loss_and_grads(L, p, "fp64", 2, u0, target)
+    b = loss_and_grads(L, p, "fp64", 100, u0, target)
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1])
+    # dJ/dnu is summed with FP64 atomics across CTAs: same value up to summation order
+    assert abs(a[2] - b[2]) <= 1e-13 * abs(a[2])
+
+
+def test_gradient_matches_central_differences_of_the_gpu_forward(L):
+    p = problem(steps=5)
+    u0 = np.stack([wl.burgers_ic(p.N, 11)])
+    target = np.stack([wl.burgers_ic(p.N, 1011)])
+    J, gu, gnu = loss_and_grads(L, p, "fp64", 2, u0, target)
+    s = solver_for(p, "fp64", 2)
+
+    def J_of(u_init, nu):
+        x = torch.tensor(u_init, dtype=torch.float64, device="cuda")
+        uT = s(x, torch.tensor(nu, dtype=torch.float64))
+        return 0.5 * p.h * float(((uT - torch.tensor(target, device="cuda")) ** 2).sum())
+
+    for i in (5, 20, 33, 58):
+        e = 1e-6
+        up, um = u0.copy(), u0.copy()
+        up[0, i] += e
+        um[0, i] -= e
+        fd = (J_of(up, p.c2) - J_of(um, p.c2)) / (2 * e)
+        assert abs(fd - gu[0, i]) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(gu)))
+    e = 1e-3 * p.c2
+    fd_nu = (J_of(u0, p.c2 + e) - J_of(u0, p.c2 - e)) / (2 * e)
+    assert abs(fd_nu - gnu) <= 1e-5 * abs(fd_nu)
