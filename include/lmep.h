@@ -167,8 +167,11 @@ typedef struct lmep_batch_desc {
   int32_t n;                 /* stencil width (odd, <= 13 for ETDRK2) */
   int32_t scheme;            /* lmep_scheme */
   int32_t nonlin;            /* lmep_nonlin (KdV not supported in batches) */
-  int32_t tile;              /* points per tile: 0 = default; else a multiple of 256 */
-  int32_t block;             /* threads per CTA: 0 = default; 128, 256 or 512 */
+  int32_t tile;              /* staged points per tile: 0 = default; else a multiple of 256.
+                                A tile updates `tile` points, or for ETDRK2
+                                tile - 2 * round_up((n - 1) / 2, 4), so that both
+                                stages split evenly over the CTA's threads. */
+  int32_t block;             /* threads per CTA: 0 = default; 64, 128, 256 or 512 */
   int32_t ctas_per_sm;       /* persistent CTAs per SM: 0 = default */
   double dt;
   lmep_operator op;          /* shared coefficients (frozen_adv must be 0) */
@@ -237,7 +240,9 @@ LMEP_API lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const
                                        const void* u_dev, int32_t* stats_dev, int32_t precision, void* stream);
 
 /* Synchronise `stream`, read and clear the device status flags.
- * Returns LMEP_ERR_NONFINITE if any kernel produced Inf/NaN since the last call. */
+ * Returns LMEP_ERR_TIMEOUT if a kernel gave up a bounded wait for one of its
+ * own bulk copies (its outputs are then incomplete), else LMEP_ERR_NONFINITE
+ * if any kernel produced Inf/NaN since the last call. */
 LMEP_API lmep_status lmep_sync_status(lmep_handle* h, void* stream);
 
 /* FMA-chain microbenchmark (all SMs): *flops_out receives achieved FLOP/s

@@ -21,7 +21,7 @@ from . import (Handle, Operator, lmep_batch_prepare, lmep_batch_workspace_bytes,
                lmep_step_batched_once, state_dtype)
 
 TILES = (1024, 2048, 4096, 8192)
-BLOCKS = (128, 256, 512)
+BLOCKS = (64, 128, 256, 512)
 CTAS = (0, 2, 4)
 
 

@@ -25,7 +25,7 @@ struct BatchPlan {
 
 struct lmep_handle {
   int device;
-  unsigned* flags;  // device status word: bit 0 = non-finite output
+  unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
   std::map<const void*, BatchPlan> plans;
 };
 
@@ -235,7 +235,8 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
     if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "stored-weight stepping takes batch <= 1 (use lmep_batch_*)");
     if (nonlin == 2 && g->bc != LMEP_BC_PERIODIC) return fail(LMEP_ERR_UNSUPPORTED, "KdV needs a periodic grid");
-    const bool fast = nonlin != 2 && g->bc != LMEP_BC_DIRICHLET;
+    // the pipelined kernel copies 16-byte aligned blocks of the state
+    const bool fast = nonlin != 2 && g->bc != LMEP_BC_DIRICHLET && aligned16(cur) && aligned16(nxt);
     const int H = fast ? lmep::apply_fast_halo(g->n, scheme) : lmep::apply_halo(g->n, scheme, nonlin, g->bc);
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
     if (g->bc == LMEP_BC_PERIODIC && g->N < H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
@@ -245,19 +246,22 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     a.n = g->n;
     a.scheme = scheme;
     a.nonlin = nonlin;
-    a.tile = default_tile(mixed);
+    a.tile = fast ? lmep::fast_tile_out(default_tile(mixed), g->n, scheme) : default_tile(mixed);
     if (g->bc == LMEP_BC_DIRICHLET && a.tile < 4 * g->n) a.tile = 4 * g->n;
     a.dt = dt;
     a.bc_lo = g->bc_lo;
     a.bc_hi = g->bc_hi;
     a.inst = nullptr;
     a.tiles = nullptr;
+    a.desc = nullptr;
+    a.ptab = nullptr;
     a.ntiles = (g->N + a.tile - 1) / a.tile;
     a.wq = 1 + scheme;
     a.w_stride = int64_t(g->n) * a.wq * g->n;
     a.N = g->N;
     a.h = g->h;
     a.bc = g->bc;
+    if (!lmep::apply_configure(a, mixed)) return fail(LMEP_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     const int block = 256;
     const int grid = lmep::apply_grid(a, block, 0, mixed);
     for (int64_t t = 0; t < nsteps; ++t) {
@@ -273,9 +277,9 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
 // ------------------------------------------------------------------ batches
 namespace {
 struct BatchLayout {
-  size_t inst_off, tiles_off, h_off, w_off, total;
+  size_t inst_off, tiles_off, desc_off, h_off, w_off, ptab_off, total;
   int64_t ntiles;
-  int tile;
+  int tile;  // points updated per tile
 };
 lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayout* L) {
   if (!d || d->B <= 0 || !d->N_host || !d->h_host || !d->bc_host) return fail(LMEP_ERR_INVALID, "bad batch descriptor");
@@ -289,9 +293,10 @@ lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayou
   const bool mixed = precision == LMEP_PREC_MIXED;
   int tile = d->tile > 0 ? d->tile : default_tile(mixed);
   if (tile % 256 != 0 || tile > 16384) return fail(LMEP_ERR_INVALID, "tile must be a multiple of 256, <= 16384");
-  if (d->block != 0 && d->block != 128 && d->block != 256 && d->block != 512)
-    return fail(LMEP_ERR_INVALID, "block must be 128, 256 or 512");
+  if (d->block != 0 && d->block != 64 && d->block != 128 && d->block != 256 && d->block != 512)
+    return fail(LMEP_ERR_INVALID, "block must be 64, 128, 256 or 512");
   const int H = lmep::apply_fast_halo(d->n, d->scheme);
+  const int tile_out = lmep::fast_tile_out(tile, d->n, d->scheme);
   int64_t ntiles = 0;
   for (int64_t b = 0; b < d->B; ++b) {
     const int64_t N = d->N_host[b];
@@ -299,17 +304,19 @@ lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayou
       return fail(LMEP_ERR_INVALID, "batch instances must be periodic or Neumann");
     if (N < 2 * H + 8 || N < d->n) return fail(LMEP_ERR_UNSUPPORTED, "instance too small for the halo");
     if (!(d->h_host[b] > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
-    ntiles += (N + tile - 1) / tile;
+    ntiles += (N + tile_out - 1) / tile_out;
   }
   if (ntiles > (int64_t(1) << 31) - 1) return fail(LMEP_ERR_INVALID, "too many tiles");
   const size_t es = mixed ? 4 : 8;
-  L->tile = tile;
+  L->tile = tile_out;
   L->ntiles = ntiles;
   L->inst_off = 256;
   L->tiles_off = align_up(L->inst_off + size_t(d->B) * sizeof(Instance), 256);
-  L->h_off = align_up(L->tiles_off + size_t(ntiles) * sizeof(int2), 256);
+  L->desc_off = align_up(L->tiles_off + size_t(ntiles) * sizeof(int2), 256);
+  L->h_off = align_up(L->desc_off + size_t(ntiles) * sizeof(lmep::TileDesc), 256);
   L->w_off = align_up(L->h_off + size_t(d->B) * sizeof(double), 256);
-  L->total = align_up(L->w_off + size_t(d->B) * d->n * (1 + d->scheme) * d->n * es, 256);
+  L->ptab_off = align_up(L->w_off + size_t(d->B) * d->n * (1 + d->scheme) * d->n * es, 256);
+  L->total = align_up(L->ptab_off + size_t(d->B) * size_t(lmep::pair_table_stride(d->n)) * es, 256);
   return LMEP_OK;
 }
 }  // namespace
@@ -334,7 +341,9 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
   const bool mixed = precision == LMEP_PREC_MIXED;
   std::vector<Instance> inst(size_t(d->B));
   std::vector<int2> tiles;
+  std::vector<lmep::TileDesc> desc;
   tiles.reserve(size_t(L.ntiles));
+  desc.reserve(size_t(L.ntiles));
   int64_t off = 0;
   for (int64_t b = 0; b < d->B; ++b) {
     inst[b].off = off;
@@ -342,7 +351,10 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
     inst[b].h = d->h_host[b];
     inst[b].bc = d->bc_host[b];
     inst[b].pad = 0;
-    for (int64_t t0 = 0; t0 < inst[b].N; t0 += L.tile) tiles.push_back(make_int2(int(b), int(t0)));
+    for (int64_t t0 = 0; t0 < inst[b].N; t0 += L.tile) {
+      tiles.push_back(make_int2(int(b), int(t0)));
+      desc.push_back(lmep::TileDesc{off, inst[b].N, t0, int32_t(b), inst[b].bc});
+    }
     off += (inst[b].N + 3) / 4 * 4;  // every instance starts on a 16-byte boundary
   }
   char* base = static_cast<char*>(ws);
@@ -350,6 +362,8 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
                      S(stream)), "copy(instances)");
   CK(cudaMemcpyAsync(base + L.tiles_off, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice,
                      S(stream)), "copy(tiles)");
+  CK(cudaMemcpyAsync(base + L.desc_off, desc.data(), desc.size() * sizeof(lmep::TileDesc), cudaMemcpyHostToDevice,
+                     S(stream)), "copy(tile descriptors)");
   CK(cudaMemcpyAsync(base + L.h_off, d->h_host, size_t(d->B) * sizeof(double), cudaMemcpyHostToDevice,
                      S(stream)), "copy(h)");
   // weights of every instance, harvested on the device
@@ -361,6 +375,8 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
   KParams p = make_params(&g, &d->op, d->dt, d->scheme);
   CK(lmep::launch_harvest_const(p, reinterpret_cast<const double*>(base + L.h_off), d->B, base + L.w_off,
                                 mixed, S(stream)), "harvest(batch)");
+  CK(lmep::launch_pair_tables(base + L.w_off, int64_t(d->n) * (1 + d->scheme) * d->n, 1 + d->scheme, d->n,
+                              d->scheme, d->B, base + L.ptab_off, mixed, S(stream)), "pair tables");
   // the host copies above read pageable vectors: make sure they are consumed
   CK(cudaStreamSynchronize(S(stream)), "sync(prepare)");
   BatchPlan plan{};
@@ -374,12 +390,15 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
   a.dt = d->dt;
   a.inst = reinterpret_cast<const Instance*>(base + L.inst_off);
   a.tiles = reinterpret_cast<const int2*>(base + L.tiles_off);
+  a.desc = reinterpret_cast<const lmep::TileDesc*>(base + L.desc_off);
+  a.ptab = base + L.ptab_off;
   a.ntiles = L.ntiles;
   a.wq = 1 + d->scheme;
   a.w_stride = int64_t(d->n) * a.wq * d->n;
   a.N = 0;
   a.h = 1.0;
   a.bc = LMEP_BC_PERIODIC;
+  if (!lmep::apply_configure(a, mixed)) return fail(LMEP_ERR_INVALID, "tile too large for shared memory");
   plan.W = base + L.w_off;
   plan.points = off;
   plan.block = d->block > 0 ? d->block : 256;
@@ -397,6 +416,7 @@ lmep_status lmep_step_batched(lmep_handle* h, const void* ws, void* u_dev, void*
   auto it = h->plans.find(ws);
   if (it == h->plans.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
   if (nsteps < 0) return fail(LMEP_ERR_INVALID, "nsteps < 0");
+  if (!aligned16(u_dev) || !aligned16(work_dev)) return fail(LMEP_ERR_INVALID, "batched states must be 16-byte aligned");
   const BatchPlan& plan = it->second;
   void* cur = u_dev;
   void* nxt = work_dev;
@@ -417,6 +437,8 @@ lmep_status lmep_step_batched_once(lmep_handle* h, const void* ws, const void* u
   if (u_in_dev == u_out_dev) return fail(LMEP_ERR_INVALID, "u_in_dev and u_out_dev must differ");
   auto it = h->plans.find(ws);
   if (it == h->plans.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
+  if (!aligned16(u_in_dev) || !aligned16(u_out_dev))
+    return fail(LMEP_ERR_INVALID, "batched states must be 16-byte aligned");
   const BatchPlan& plan = it->second;
   CK(lmep::launch_apply(plan.ap, u_in_dev, u_out_dev, plan.W, plan.mixed, plan.block, plan.grid, h->flags,
                         S(stream)),
@@ -477,6 +499,7 @@ lmep_status lmep_sync_status(lmep_handle* h, void* stream) {
   CK(cudaMemcpy(&flags, h->flags, sizeof(unsigned), cudaMemcpyDeviceToHost), "read status");
   if (flags) {
     CK(cudaMemset(h->flags, 0, sizeof(unsigned)), "clear status");
+    if (flags & 2u) return fail(LMEP_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy");
     return fail(LMEP_ERR_NONFINITE, "a kernel produced a non-finite value");
   }
   return LMEP_OK;

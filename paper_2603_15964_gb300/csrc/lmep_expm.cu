@@ -20,6 +20,7 @@ DeviceInfo device_info() {
   cudaGetDevice(&dev);
   if (dev != dev_cached) {
     cudaDeviceGetAttribute(&info.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&info.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     dev_cached = dev;
   }
   return info;

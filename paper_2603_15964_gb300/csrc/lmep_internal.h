@@ -28,6 +28,7 @@ void set_last_error(const std::string& msg);
 
 struct DeviceInfo {
   int sms;
+  int smem_optin;  // dynamic shared memory a CTA may opt in to (bytes)
 };
 DeviceInfo device_info();
 
@@ -51,15 +52,28 @@ struct Instance {
   int bc;
   int pad;
 };
+// One tile of a batch: instance offset, length and boundary condition, and the
+// tile's first point (32 bytes, read as two 16-byte vectors).
+struct TileDesc {
+  int64_t off;
+  int64_t N;
+  int64_t t0;
+  int32_t b;
+  int32_t bc;
+};
+static_assert(sizeof(TileDesc) == 32, "TileDesc is 32 bytes");
 struct ApplyParams {
   int n, scheme, nonlin, tile;
   int halo;          // staged halo per side (apply_halo / apply_fast_halo)
-  int fast;          // 1: register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
+  int fast;          // 1: pipelined register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
+  int stages;        // fast kernel: stage buffers (set by apply_configure)
   double dt;
   double bc_lo, bc_hi;
   // instance table (device) and tile table (device, int2 = {instance, start})
   const Instance* inst;
   const int2* tiles;
+  const TileDesc* desc;  // fast kernel: tile descriptors (nullptr: one instance)
+  const void* ptab;      // fast kernel: per-instance weight-pair tables (nullptr: one instance)
   int64_t ntiles;
   int64_t w_stride;  // elements between the weight blocks of consecutive instances
   int wq;            // weight rows stored per row class (1 + n_phi)
@@ -70,10 +84,18 @@ struct ApplyParams {
 };
 int apply_halo(int n, int scheme, int nonlin, int bc);
 int apply_fast_halo(int n, int scheme);
+int fast_tile_out(int tile, int n, int scheme);
 size_t apply_smem_bytes(int tile, int halo, int scheme, bool mixed);
 cudaError_t launch_apply(const ApplyParams& a, const void* u, void* out, const void* W, bool mixed,
                          int block, int grid, unsigned* flags, cudaStream_t s);
 int apply_grid(const ApplyParams& a, int block, int ctas_per_sm, bool mixed);
+// Choose the fast kernel's pipeline depth; false if the tile does not fit in shared memory.
+bool apply_configure(ApplyParams& a, bool mixed);
+// Weight-pair tables of the fast kernel (elements per instance, and the kernel
+// that fills B of them from harvested weights).
+int pair_table_stride(int n);
+cudaError_t launch_pair_tables(const void* W, int64_t w_stride, int wq, int n, int scheme, int64_t B, void* tab,
+                               bool mixed, cudaStream_t s);
 
 // ---- adjoint (lmep_adjoint.cu)
 size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed);

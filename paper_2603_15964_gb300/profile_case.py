@@ -1,7 +1,15 @@
-"""Small profiling case: warm-up, then one fused frozen-velocity Burgers step
-(N = 65536, n = 13, CFL = 4, nu = 1e-6, departure-centred) in the FP32 form
-and one in FP64.  Used with `ncu -k regex:k_warp -s 4 -c 2` (the two launches
-after four warm-up launches)."""
+"""Small profiling cases.
+
+`python -m paper_2603_15964_gb300.profile_case [n cfl]`: warm-up, then one
+fused frozen-velocity Burgers step (N = 65536, n = 13, CFL = 4, nu = 1e-6,
+departure-centred) in the FP32 form and one in FP64.  Used with
+`ncu -k regex:k_warp -s 4 -c 2` (the two launches after four warm-up launches).
+
+`python -m paper_2603_15964_gb300.profile_case ac [tile block]`: the batched
+Allen-Cahn ETDRK2 step (4096 instances, N log-uniform in [1024, 65536],
+n = 9, FP32 state, 254 MB): three warm-up steps, then one step.  Used with
+`ncu -k regex:k_apply -s 3 -c 1`.
+"""
 import os
 import sys
 
@@ -31,5 +39,28 @@ def main(n: int = 13, cfl: float = 4.0) -> None:
     print("profile case ok")
 
 
+def allen_cahn(tile: int = 2048, block: int = 128) -> None:
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    import workloads as wl
+    from paper_2603_15964_gb300.batch import BatchedProblem, LaunchShape
+
+    batch = wl.allen_cahn_batch()
+    hs = [batch.problem(b).h for b in range(len(batch.Ns))]
+    prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, batch.scheme, "allen_cahn", batch.dt,
+                          L.Operator(c2=batch.eps2), "mixed", LaunchShape(tile, block, 0))
+    u = prob.empty_state().uniform_(-0.1, 0.1)
+    w = torch.empty_like(u)
+    for t in range(4):                                    # three warm-up steps, then the profiled one
+        L.lmep_step_batched_once(prob.handle, prob.workspace, u if t % 2 == 0 else w, w if t % 2 == 0 else u)
+    L.lmep_sync_status(prob.handle)
+    torch.cuda.synchronize()
+    print("profile case ok")
+
+
 if __name__ == "__main__":
-    main(*(float(a) if i else int(a) for i, a in enumerate(sys.argv[1:])))
+    if len(sys.argv) > 1 and sys.argv[1] == "ac":
+        allen_cahn(*(int(a) for a in sys.argv[2:]))
+    else:
+        main(*(float(a) if i else int(a) for i, a in enumerate(sys.argv[1:])))

@@ -83,3 +83,28 @@ def test_autotune_picks_a_candidate(L, tmp_path, monkeypatch):
     again, t2 = autotune(batch.Ns, hs, batch.bcs, 9, "etdrk2", "allen_cahn", batch.dt,
                          L.Operator(c2=batch.eps2), "mixed", candidates=cands)
     assert again == best and t2 == timings                       # served from the cache
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_launch_shapes_agree_bit_for_bit(L, precision):
+    """Every output is the same sequence of operations whatever the tile size,
+    block size or pipeline depth, so all launch shapes give identical states."""
+    from paper_2603_15964_gb300.batch import BatchedProblem, LaunchShape, pack, unpack
+    batch = wl.allen_cahn_batch(B=9, Nmin=60, Nmax=9000, n=9, scheme="etdrk2", steps=3, seed=11)
+    hs = [batch.problem(b).h for b in range(len(batch.Ns))]
+    u0s = [wl.allen_cahn_ic(int(N), 50 + b) for b, N in enumerate(batch.Ns)]
+    results = []
+    for tile, block in ((1024, 64), (2048, 128), (4096, 256), (2048, 512), (1024, 512)):
+        prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt,
+                              L.Operator(c2=batch.eps2), precision, LaunchShape(tile, block))
+        u = pack(u0s, L.state_dtype(precision))
+        prob.step(u, torch.empty_like(u), batch.steps)
+        L.lmep_sync_status(prob.handle)
+        results.append(unpack(u, batch.Ns))
+    for r in results[1:]:
+        for b in range(len(batch.Ns)):
+            assert np.array_equal(r[b], results[0][b])
+    for b in (0, len(batch.Ns) - 1):
+        want = olmep.run(batch.problem(b), u0s[b] if precision == "fp64" else
+                         u0s[b].astype(np.float32).astype(np.float64), batch.steps)
+        assert rel_linf(results[0][b], want) <= tol(precision) * batch.steps
