@@ -412,7 +412,7 @@ def allen_cahn_main(args, rank, world, local_rank, cores):
     op = L.Operator(c2=batch.eps2)
     from paper_2603_15964_gb300.batch import pack
     u0s = [wl.allen_cahn_ic(int(batch.Ns[b]), b) for b in range(B)]
-    cands = [LaunchShape(t, bl, 0) for t in (1024, 2048, 4096) for bl in (64, 128, 256)]
+    cands = [LaunchShape(t, bl, 0) for t in (256, 512, 1024, 2048) for bl in (64, 128, 256)]
     shape, timings = autotune(batch.Ns, hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",
                               candidates=cands, use_cache=False)
     prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",

@@ -167,10 +167,13 @@ typedef struct lmep_batch_desc {
   int32_t n;                 /* stencil width (odd, <= 13 for ETDRK2) */
   int32_t scheme;            /* lmep_scheme */
   int32_t nonlin;            /* lmep_nonlin (KdV not supported in batches) */
-  int32_t tile;              /* staged points per tile: 0 = default; else a multiple of 256.
-                                A tile updates `tile` points, or for ETDRK2
-                                tile - 2 * round_up((n - 1) / 2, 4), so that both
-                                stages split evenly over the CTA's threads. */
+  int32_t tile;              /* staged points per warp tile: 0 = default; else a multiple
+                                of 128 (one round of 128 points per 32 lanes).  A tile
+                                updates `tile` points, or for ETDRK2
+                                (tile / 128) * (128 - 2 * round_up((n - 1) / 2, 4)):
+                                the first stage of a round spans its updated points
+                                plus one stencil halo on each side.  A tile too large
+                                for 3 slots per warp in shared memory is rejected. */
   int32_t block;             /* threads per CTA: 0 = default; 64, 128, 256 or 512 */
   int32_t ctas_per_sm;       /* persistent CTAs per SM: 0 = default */
   double dt;

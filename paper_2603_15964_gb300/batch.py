@@ -17,12 +17,12 @@ from dataclasses import dataclass, field
 
 import torch
 
-from . import (Handle, Operator, lmep_batch_prepare, lmep_batch_workspace_bytes, lmep_step_batched,
+from . import (Handle, LmepError, Operator, lmep_batch_prepare, lmep_batch_workspace_bytes, lmep_step_batched,
                lmep_step_batched_once, state_dtype)
 
-TILES = (1024, 2048, 4096, 8192)
-BLOCKS = (64, 128, 256, 512)
-CTAS = (0, 2, 4)
+TILES = (256, 512, 1024, 2048)
+BLOCKS = (64, 128, 256)
+CTAS = (0,)
 
 
 def batch_offsets(Ns) -> list:
@@ -159,7 +159,10 @@ def autotune(Ns, hs, bcs, n, scheme, nonlin, dt, op: Operator, precision: str = 
     best, best_ms = None, float("inf")
     u = work = None
     for sh in candidates:
-        prob = BatchedProblem(Ns, hs, bcs, n, scheme, nonlin, dt, op, precision, sh, handle)
+        try:
+            prob = BatchedProblem(Ns, hs, bcs, n, scheme, nonlin, dt, op, precision, sh, handle)
+        except LmepError:                      # shape does not fit this GPU's shared memory
+            continue
         if u is None:
             u = prob.empty_state().uniform_(-0.1, 0.1)
             work = torch.empty_like(u)

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblmep.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["lmep_expm_f64.cu", "lmep_expm_f32.cu", "lmep_adjoint.cu", "lmep_api.cu", "lmep_expm.cu",
-           "lmep_apply.cu", "lmep_peak.cu", "lmep_noalloc.cu"]
+           "lmep_apply.cu", "lmep_apply_stream.cu", "lmep_peak.cu", "lmep_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]

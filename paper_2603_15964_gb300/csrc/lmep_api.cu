@@ -97,6 +97,8 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int default_tile(bool mixed) { return mixed ? 2048 : 1024; }
+// staged points per warp tile of the streaming kernel (4 slots per warp fit)
+int default_fast_tile(bool mixed) { return mixed ? 1024 : 512; }
 
 }  // namespace
 
@@ -246,7 +248,7 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     a.n = g->n;
     a.scheme = scheme;
     a.nonlin = nonlin;
-    a.tile = fast ? lmep::fast_tile_out(default_tile(mixed), g->n, scheme) : default_tile(mixed);
+    a.tile = fast ? lmep::fast_tile_out(default_fast_tile(mixed), g->n, scheme) : default_tile(mixed);
     if (g->bc == LMEP_BC_DIRICHLET && a.tile < 4 * g->n) a.tile = 4 * g->n;
     a.dt = dt;
     a.bc_lo = g->bc_lo;
@@ -261,8 +263,8 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     a.N = g->N;
     a.h = g->h;
     a.bc = g->bc;
-    if (!lmep::apply_configure(a, mixed)) return fail(LMEP_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     const int block = 256;
+    if (!lmep::apply_configure(a, mixed, block)) return fail(LMEP_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     const int grid = lmep::apply_grid(a, block, 0, mixed);
     for (int64_t t = 0; t < nsteps; ++t) {
       CK(lmep::launch_apply(a, cur, nxt, W_dev, mixed, block, grid, h->flags, S(stream)), "step(apply)");
@@ -291,8 +293,8 @@ lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayou
   lmep_status st = check_prec(precision);
   if (st != LMEP_OK) return st;
   const bool mixed = precision == LMEP_PREC_MIXED;
-  int tile = d->tile > 0 ? d->tile : default_tile(mixed);
-  if (tile % 256 != 0 || tile > 16384) return fail(LMEP_ERR_INVALID, "tile must be a multiple of 256, <= 16384");
+  int tile = d->tile > 0 ? d->tile : default_fast_tile(mixed);
+  if (tile % 128 != 0 || tile > 16384) return fail(LMEP_ERR_INVALID, "tile must be a multiple of 128, <= 16384");
   if (d->block != 0 && d->block != 64 && d->block != 128 && d->block != 256 && d->block != 512)
     return fail(LMEP_ERR_INVALID, "block must be 64, 128, 256 or 512");
   const int H = lmep::apply_fast_halo(d->n, d->scheme);
@@ -398,10 +400,10 @@ lmep_status lmep_batch_prepare(lmep_handle* h, const lmep_batch_desc* d, void* w
   a.N = 0;
   a.h = 1.0;
   a.bc = LMEP_BC_PERIODIC;
-  if (!lmep::apply_configure(a, mixed)) return fail(LMEP_ERR_INVALID, "tile too large for shared memory");
+  plan.block = d->block > 0 ? d->block : 256;
+  if (!lmep::apply_configure(a, mixed, plan.block)) return fail(LMEP_ERR_INVALID, "tile too large for shared memory");
   plan.W = base + L.w_off;
   plan.points = off;
-  plan.block = d->block > 0 ? d->block : 256;
   plan.mixed = mixed;
   plan.grid = lmep::apply_grid(a, plan.block, d->ctas_per_sm, mixed);
   plan.bytes = L.total;

@@ -66,7 +66,8 @@ struct ApplyParams {
   int n, scheme, nonlin, tile;
   int halo;          // staged halo per side (apply_halo / apply_fast_halo)
   int fast;          // 1: pipelined register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
-  int stages;        // fast kernel: stage buffers (set by apply_configure)
+  int stages;        // fast kernel: stage slots per warp (set by apply_configure)
+  int warp_smem;     // fast kernel: shared-memory bytes per warp (set by apply_configure)
   double dt;
   double bc_lo, bc_hi;
   // instance table (device) and tile table (device, int2 = {instance, start})
@@ -89,8 +90,14 @@ size_t apply_smem_bytes(int tile, int halo, int scheme, bool mixed);
 cudaError_t launch_apply(const ApplyParams& a, const void* u, void* out, const void* W, bool mixed,
                          int block, int grid, unsigned* flags, cudaStream_t s);
 int apply_grid(const ApplyParams& a, int block, int ctas_per_sm, bool mixed);
-// Choose the fast kernel's pipeline depth; false if the tile does not fit in shared memory.
-bool apply_configure(ApplyParams& a, bool mixed);
+// Choose the fast kernel's pipeline depth for `block` threads per CTA; false
+// if the tile does not fit in shared memory.
+bool apply_configure(ApplyParams& a, bool mixed, int block);
+// ---- warp-streaming apply (lmep_apply_stream.cu)
+constexpr int STREAM_MAX_STAGES = 4;
+constexpr int STREAM_HEADER = 8 * STREAM_MAX_STAGES + 32 * STREAM_MAX_STAGES;  // mbarriers, tile descriptors
+const void* stream_kernel(int scheme, int n, bool mixed);
+size_t stream_warp_smem(const ApplyParams& a, bool mixed, int stages, int scheme);
 // Weight-pair tables of the fast kernel (elements per instance, and the kernel
 // that fills B of them from harvested weights).
 int pair_table_stride(int n);

@@ -39,7 +39,7 @@ def main(n: int = 13, cfl: float = 4.0) -> None:
     print("profile case ok")
 
 
-def allen_cahn(tile: int = 2048, block: int = 128) -> None:
+def allen_cahn(tile: int = 1024, block: int = 128) -> None:
     import torch
 
     import paper_2603_15964_gb300 as L

@@ -76,7 +76,7 @@ def test_autotune_picks_a_candidate(L, tmp_path, monkeypatch):
     monkeypatch.setenv("LMEP_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     batch = small_batch(B=40)
     hs = [batch.problem(b).h for b in range(40)]
-    cands = [LaunchShape(1024, 256, 0), LaunchShape(2048, 512, 0), LaunchShape(4096, 128, 2)]
+    cands = [LaunchShape(512, 256, 0), LaunchShape(1024, 128, 0), LaunchShape(256, 64, 2)]
     best, timings = autotune(batch.Ns, hs, batch.bcs, 9, "etdrk2", "allen_cahn", batch.dt,
                              L.Operator(c2=batch.eps2), "mixed", candidates=cands)
     assert best in cands and len(timings) == 3 and all(v > 0 for v in timings.values())
@@ -94,7 +94,7 @@ def test_launch_shapes_agree_bit_for_bit(L, precision):
     hs = [batch.problem(b).h for b in range(len(batch.Ns))]
     u0s = [wl.allen_cahn_ic(int(N), 50 + b) for b, N in enumerate(batch.Ns)]
     results = []
-    for tile, block in ((1024, 64), (2048, 128), (4096, 256), (2048, 512), (1024, 512)):
+    for tile, block in ((256, 64), (512, 128), (1024, 256), (2048, 128), (128, 512)):
         prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt,
                               L.Operator(c2=batch.eps2), precision, LaunchShape(tile, block))
         u = pack(u0s, L.state_dtype(precision))
