@@ -48,6 +48,11 @@ NU = 1e-6
 PI_M = {3: 2, 5: 3, 7: 4, 9: 5, 13: 6}          # matrix products of Pade [m/m] (Higham 2005)
 P32_NOMINAL = 152 * 128 * 2 * 2.07e9             # FP32 FMA lanes x 2 x max SM clock
 P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
+# DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of the
+# current kernels (profiles/k_warp_frozen_burgers_N65536_n13_cfl4.md and
+# profiles/k_apply_stream_allen_cahn_batch4096_n9.md); set to None when a kernel changes.
+TRAFFIC_K_WARP_13_FLOAT = 6.397696e6 + 0.717824e6
+TRAFFIC_K_APPLY_STREAM_AC = 253.765632e6 + 196.658688e6
 
 
 def workload_config(rank_seed: int = 0) -> dict:
@@ -94,7 +99,10 @@ def oracle_pool(cores: int):
 
 
 def sample_points(per_instance: int, salt: int):
+    """`per_instance` seeded random interior points, or every interior point if it is 0."""
     import numpy as np
+    if per_instance <= 0 or per_instance >= N_POINTS - 2:
+        return list(range(1, N_POINTS - 1))
     rng = np.random.default_rng(1234 + salt)
     return sorted(set(rng.integers(1, N_POINTS - 1, per_instance).tolist()))
 
@@ -467,14 +475,20 @@ def allen_cahn_main(args, rank, world, local_rank, cores):
     achieved = bytes_launch / (per_launch_ms * 1e-3) / 1e9
     cpu = err = None
     if pool is not None:
-        small = [int(b) for b in np.argsort(batch.Ns)[: max(cores, 4)]]
+        small, acc = [], 0
+        for b in range(B):                  # whole instances in batch order (the batch's size mix)
+            if acc >= args.cpu_points:
+                break
+            small.append(b)
+            acc += int(batch.Ns[b])
         t0 = time.perf_counter()
-        outs = pool.map(_oracle_ac, [(B, b, rank) for b in small])
+        outs = pool.map(_oracle_ac, [(B, b, rank) for b in small], chunksize=1)
         dt = time.perf_counter() - t0
         pool.close()
         npts = sum(int(batch.Ns[b]) for b in small)
         cpu = {"value": npts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"one ETDRK2 step of the {len(small)} smallest instances ({npts} point-updates)"}
+               "sample": f"one ETDRK2 step of the first {len(small)} instances of the batch "
+                         f"({npts} point-updates, {dt:.1f} s)"}
         worst = 0.0
         for b, want in zip(small, outs):
             got = first[prob.offsets[b]:prob.offsets[b] + int(batch.Ns[b])]
@@ -483,10 +497,13 @@ def allen_cahn_main(args, rank, world, local_rank, cores):
     line = {"metric": METRIC, "value": pts / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": allen_cahn_config(B, batch),
-            "error": {"vs": "FP64 oracle, one step, smallest instances", "rel_linf": err},
+            "error": {"vs": "FP64 oracle, one step, the cpu_baseline instances", "rel_linf": err},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_apply<float, ETDRK2, Allen-Cahn> (one persistent launch per step)",
+                         "frac": achieved / peak, "traffic": TRAFFIC_K_APPLY_STREAM_AC,
+                         "traffic_unit": "bytes per launch (ncu, tile 1024 / block 128 capture; below the "
+                                         "algorithmic bytes because part of u+ is still in L2 at the end)",
+                         "peak_source": peak_src,
+                         "kernel": "k_apply_stream<float, ETDRK2, n = 9> (one persistent launch per step)",
                          "algorithmic_bytes_per_launch": bytes_launch},
             "autotune": {"chosen": shape.__dict__, "ms_per_step": timings},
             "cpu_baseline": cpu,
@@ -510,7 +527,10 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
-    ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle points per instance (cpu_baseline)")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="oracle points per instance for cpu_baseline (0: every interior point of the step)")
+    ap.add_argument("--cpu-points", type=float, default=12e6,
+                    help="Allen-Cahn cpu_baseline: oracle point-updates (whole instances in batch order)")
     ap.add_argument("--workload", choices=["burgers", "allen_cahn"], default="burgers",
                     help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply")
     ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
@@ -564,9 +584,10 @@ def main():
     if pool is not None:
         tasks, vals, npts, dt = run_oracle_sample(pool, cores, 0, args.cpu_sample)
         pool.close()
+        what = (f"{args.cpu_sample} random interior points of each of the 9 instances" if args.cpu_sample > 0
+                else "every interior point of the 9 instances")
         cpu = {"value": npts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_sample} random interior points of each of the 9 instances, one step "
-                         f"({npts} point-updates, {dt:.1f} s)"}
+               "sample": f"{what}, one step ({npts} point-updates, {dt:.1f} s)"}
         err = stated_error(res, tasks, vals)
     m = res["mixed"]
     t13 = m["t13"]
@@ -581,7 +602,8 @@ def main():
         "error": {"vs": "FP64 oracle, one step from the initial state, sampled points (cpu_baseline sample)",
                   "rel_linf": err},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / p64, "traffic": None,
+                     "frac": achieved / p64, "traffic": TRAFFIC_K_WARP_13_FLOAT,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "kernel": "k_warp<13,float> (frozen-velocity fused step, n = 13)",
                      "note": "FP64-equivalent rate (F64 + F32 * P64/P32) / t of the algorithm's own FLOPs; "
                              "peak = GB300 nominal FP64; see measured FMA-chain peaks",
