@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
   double dnu_acc = 0.0;
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
   for (int64_t it = int64_t(blockIdx.x) * AW + warp; it < items; it += int64_t(gridDim.x) * AW) {
-    const int64_t bb = it / p.N;
-    const int64_t i = it - bb * p.N;
+    int64_t bb, i;
+    split_index(it, p.N, p.batch, bb, i);
     const ST* ub = u + bb * p.N;
     if (dir && (i == 0 || i == p.N - 1)) {
       for (int j = lane; j < n; j += 32) Wout[it * n + j] = ST(0);

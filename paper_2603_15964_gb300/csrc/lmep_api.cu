@@ -89,6 +89,9 @@ KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int 
   p.c0dt = dt * op->c0;
   p.c2h = dt * op->c2 / (g->h * g->h);
   p.c3h = dt * op->c3 / (g->h * g->h * g->h);
+  p.c0dt_f = float(p.c0dt);
+  p.c2h_f = float(p.c2h);
+  p.c3h_f = float(p.c3h);
   return p;
 }
 
@@ -136,6 +139,11 @@ lmep_status lmep_create(lmep_handle** out) {
   if (e != cudaSuccess) {
     cudaFree(flags);
     return cuda_fail(e, "cudaMemset(status)");
+  }
+  e = lmep::fornberg_init();  // before any stream capture that may use the handle
+  if (e != cudaSuccess) {
+    cudaFree(flags);
+    return cuda_fail(e, "derivative tables");
   }
   lmep_handle* h = new lmep_handle();
   h->device = dev;

@@ -90,13 +90,16 @@ __device__ inline void fornberg_row(double z, int n, double c[4][DMAX]) {
 // Fill Dh[k-1][i*LD + j] = h^k D^(k)[i][j] (k = 1..3) for the uniform window of
 // width n in shared memory.  Threads 0..n-1 of the block each build one row.
 // Caller synchronises.
-__device__ inline void fornberg_block(double* Dh, int n) {
+__device__ inline void fornberg_block(double* Dh, int n, float* Dhf = nullptr) {
   const int t = threadIdx.x;
   if (t < n) {
     double c[4][DMAX];
     fornberg_row(double(t), n, c);
     for (int k = 1; k <= 3; ++k)
-      for (int j = 0; j < n; ++j) Dh[(k - 1) * DMAX * LD + t * LD + j] = c[k][j];
+      for (int j = 0; j < n; ++j) {
+        Dh[(k - 1) * DMAX * LD + t * LD + j] = c[k][j];
+        if (Dhf) Dhf[(k - 1) * DMAX * LD + t * LD + j] = float(c[k][j]);
+      }
   }
 }
 
@@ -114,6 +117,11 @@ __device__ __forceinline__ int64_t window_start(int64_t i, int64_t N, int n, int
 // Map a possibly out-of-range index to the grid (periodic wrap, even reflection).
 __device__ __forceinline__ int64_t grid_index(int64_t q, int64_t N, int bc) {
   if (bc == BC_PERIODIC) {
+    // a window (n <= N nodes) wraps at most once; the general remainder (a
+    // slow 64-bit division) only runs for indices further away
+    if (q >= 0 && q < N) return q;
+    if (q < 0 && q >= -N) return q + N;
+    if (q >= N && q < 2 * N) return q - N;
     q %= N;
     return q < 0 ? q + N : q;
   }
@@ -124,16 +132,40 @@ __device__ __forceinline__ int64_t grid_index(int64_t q, int64_t N, int bc) {
   }
   return q;
 }
+// it = b N + i with 0 <= i < N: no division for one instance, a 32-bit one
+// when the index fits, the 64-bit division otherwise.
+__device__ __forceinline__ void split_index(int64_t it, int64_t N, int64_t batch, int64_t& b, int64_t& i) {
+  if (batch <= 1) {
+    b = 0;
+    i = it;
+  } else if (it < (int64_t(1) << 32) && N < (int64_t(1) << 32)) {
+    const uint32_t q = uint32_t(it) / uint32_t(N);
+    b = q;
+    i = it - int64_t(q) * N;
+  } else {
+    b = it / N;
+    i = it - b * N;
+  }
+}
+
 // Departure-centring shift clamp(floor(u dt / h + 1/2), -hs, hs), evaluated
 // with explicitly rounded FP64 operations, (u dt) / h + 1/2, so that the
 // integer decision is reproducible bit for bit.  dt_h = dt / h gives a cheap
 // estimate first; the exact division runs only when the estimate lies within
 // 1e-9 of an integer, where the two roundings could disagree.
+// Rare-path helpers kept out of line: inlined, the compiler may turn these
+// long FP64 sequences into predicated code that occupies the FP64 pipe on
+// every call even when the branch is not taken.
+static __device__ __noinline__ double departure_exact(double u, double dt, double h) {
+  return __dadd_rn(__ddiv_rn(__dmul_rn(u, dt), h), 0.5);
+}
+static __device__ __noinline__ double drcp_slow(double x) { return __drcp_rn(x); }
+
 __device__ __forceinline__ int departure_shift(double u, double dt, double h, int n, double dt_h) {
   const int hs = (n - 1) >> 1;
   double t = fma(u, dt_h, 0.5);
   const double f = t - floor(t);
-  if (!(f > 1e-9 && f < 1.0 - 1e-9)) t = __dadd_rn(__ddiv_rn(__dmul_rn(u, dt), h), 0.5);
+  if (!(f > 1e-9 && f < 1.0 - 1e-9)) t = departure_exact(u, dt, h);
   // fmin/fmax return the non-NaN operand, so a non-finite state still gives a
   // window inside the clamp range (the non-finite result is flagged later).
   const double k = fmax(double(-hs), fmin(double(hs), floor(t)));
@@ -415,7 +447,7 @@ template <int STEPS>
 __device__ __forceinline__ double recip_nr(double x) {
   const int hi = __double2hiint(x);
   const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
-  if (e <= 1 || e >= 253) return __drcp_rn(x);
+  if (e <= 1 || e >= 253) return drcp_slow(x);
   const float xf = __int_as_float((hi & int(0x80000000)) | (e << 23) | ((hi & 0xfffff) << 3));
   const int rb = __float_as_int(__frcp_rn(xf));
   const int re = ((rb >> 23) & 0xff) - 127 + 1023;
@@ -425,11 +457,16 @@ __device__ __forceinline__ double recip_nr(double x) {
   return r;
 }
 
-// Solve Q R = P in place on G = [Q | P] by Gauss-Jordan elimination with
-// partial pivoting (FP64).  On return G[:, D:2D] holds R.  Pivot magnitudes
-// are compared as IEEE bit patterns (monotonic for non-negative doubles).
-template <int D, int NEWTON = 2>
-__device__ void gauss_jordan(double* G, int lane, int ncols = 2 * D) {
+// Solve Q R = P in place on G = [Q | P] (NC = D + number of right-hand
+// sides <= 32 columns) by Gauss-Jordan elimination with partial pivoting
+// (FP64).  On return G[:, D:NC] holds R.  Pivot magnitudes are compared as
+// IEEE bit patterns (monotonic for non-negative doubles).  The step loop is
+// unrolled, so every step's element count and index divisions are constants
+// and each step issues exactly ceil((D - 1)(NC - k - 1) / 32) FP64 FMAs.
+template <int D, int NEWTON, int NC>
+__device__ void gauss_jordan(double* G, int lane) {
+  static_assert(NC <= 32, "one column per lane for swaps and scaling");
+#pragma unroll
   for (int k = 0; k < D; ++k) {
     long long key = -1;
     int idx = k;
@@ -446,26 +483,27 @@ __device__ void gauss_jordan(double* G, int lane, int ncols = 2 * D) {
         idx = oi;
       }
     }
-    if (idx != k) {
-      for (int j = k + lane; j < ncols; j += 32) {
-        const double a = G[k * LDG + j];
-        G[k * LDG + j] = G[idx * LDG + j];
-        G[idx * LDG + j] = a;
-      }
+    if (idx != k && k + lane < NC) {
+      const int j = k + lane;
+      const double a = G[k * LDG + j];
+      G[k * LDG + j] = G[idx * LDG + j];
+      G[idx * LDG + j] = a;
     }
     __syncwarp();
     const double inv = recip_nr<NEWTON>(G[k * LDG + k]);
-    for (int j = k + 1 + lane; j < ncols; j += 32) G[k * LDG + j] *= inv;
+    if (k + 1 + lane < NC) G[k * LDG + k + 1 + lane] *= inv;
     __syncwarp();
-    const int nc = ncols - k - 1;
+    const int nc = NC - k - 1;
     const int tot = (D - 1) * nc;
-    const float rnc = 1.0f / float(nc);
-    for (int e = lane; e < tot; e += 32) {
-      const int ii = __float2int_rz((float(e) + 0.5f) * rnc);
-      const int jj = e - ii * nc;
-      const int i = ii + (ii >= k ? 1 : 0);
-      const int j = k + 1 + jj;
-      G[i * LDG + j] = fma(-G[i * LDG + k], G[k * LDG + j], G[i * LDG + j]);
+#pragma unroll
+    for (int q = 0; q < (tot + 31) / 32; ++q) {
+      const int e = lane + 32 * q;
+      if (e < tot) {
+        const int ii = e / nc;
+        const int i = ii + (ii >= k ? 1 : 0);
+        const int j = k + 1 + (e - ii * nc);
+        G[i * LDG + j] = fma(-G[i * LDG + k], G[k * LDG + j], G[i * LDG + j]);
+      }
     }
     __syncwarp();
   }
@@ -515,6 +553,48 @@ __device__ __forceinline__ void rows_times(double* V, const double* R, int ldr, 
   __syncwarp();
 }
 
+// float -> double with integer operations only (exact): the FP64 pipe, which
+// also executes the hardware conversion, stays free.  Zero, subnormal, Inf
+// and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const int b = __float_as_int(f);
+  const int e = (b >> 23) & 0xff;
+  if (e == 0 || e == 0xff) {
+    if ((b & 0x7fffffff) == 0) return __hiloint2double(b & int(0x80000000), 0);
+    return double(f);
+  }
+  return __hiloint2double((b & int(0x80000000)) | ((e + 896) << 20) | ((b & 0x7fffff) >> 3), (b & 7) << 29);
+}
+
+// X = cI I + c1h Dh1 + c2h Dh2 + c3h Dh3 on the n x n window (zero-padded to
+// D) from the window's derivative matrices Dh (stride LD, DMAX rows per
+// order), in FP64 and, for the FP32 form, directly in FP32 from an FP32 copy
+// of Dh.  The FP32 form assembles X in FP32 and needs the FP64 matrix only
+// to settle a Pade degree next to a threshold.
+struct Asm {
+  const double* Dh;
+  const float* Dhf;
+  int n;
+  double cI, c1h, c2h, c3h;
+  float cIf, c1f, c2f, c3f;
+};
+
+template <int D>
+__device__ __forceinline__ void assemble64(double* X64, const Asm& a, int lane) {
+  for (int e = lane; e < D * D; e += 32) {
+    const int i = e / D, j = e - (e / D) * D;
+    double x = 0.0;
+    if (i < a.n && j < a.n) {
+      const int o = i * LD + j;
+      x = a.c1h * a.Dh[o];
+      x = fma(a.c2h, a.Dh[DMAX * LD + o], x);
+      if (a.c3h != 0.0) x = fma(a.c3h, a.Dh[2 * DMAX * LD + o], x);
+      if (i == j) x += a.cI;
+    }
+    X64[i * LD + j] = x;
+  }
+}
+
 // |x| as a float from the top word of a double with integer operations only
 // (exponent rebias, mantissa truncated to 20 bits; relative error < 2^-20).
 // Used where only a magnitude estimate is needed, to keep the FP64 pipe free.
@@ -542,7 +622,8 @@ __device__ __forceinline__ double norm1_smem(const T* M, int lane) {
 // and scaling s.  m = 13 uses the Al-Mohy & Higham (2009) choice of s (see the
 // file header); the powers are then scaled by exact powers of two.
 template <int D, typename PT>
-__device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lane, double nrm, int& m, int& s) {
+__device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lane, double nrm, float nrmf,
+                                   bool exact64, int& m, int& s) {
   constexpr int S = Lay<D, PT>::N;
   constexpr int LM = Lay<D, PT>::LDM;
   PT* X = w.M(0);
@@ -552,16 +633,28 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
   PT* T = w.M(4);
   PT acc[S];
   s = 0;
-  if (nrm <= THETA3) m = 3;
-  else if (nrm <= THETA5) m = 5;
-  else if (nrm <= THETA7) m = 7;
-  else if (nrm <= THETA9) m = 9;
-  else m = 13;
+  // The FP32 form decides on its FP32 norm (at least 1e-4 relative away from
+  // every threshold, so the decision equals the FP64 one); exact64 marks an
+  // FP64 norm, compared in FP64.
+  const bool f32dec = sizeof(PT) == 4 && !exact64;
+  if (f32dec) {
+    if (nrmf <= float(THETA3)) m = 3;
+    else if (nrmf <= float(THETA5)) m = 5;
+    else if (nrmf <= float(THETA7)) m = 7;
+    else if (nrmf <= float(THETA9)) m = 9;
+    else m = 13;
+  } else {
+    if (nrm <= THETA3) m = 3;
+    else if (nrm <= THETA5) m = 5;
+    else if (nrm <= THETA7) m = 7;
+    else if (nrm <= THETA9) m = 9;
+    else m = 13;
+  }
   // Norms of powers overflow FP32 for very large ||X||: there, and for
   // non-finite input, scale by the norm first (Higham 2005) and stop.
-  const bool by_norm = m == 13 && !(nrm <= 8192.0);
+  const bool by_norm = m == 13 && (f32dec ? !(nrmf <= 8192.0f) : !(nrm <= 8192.0));
   if (by_norm) {
-    double t = nrm;
+    double t = f32dec ? double(nrmf) : nrm;
     while (t > THETA13 && s < 1023) { t *= 0.5; ++s; }
     const PT sc = PT(ldexp(1.0, -s));
 #pragma unroll
@@ -583,6 +676,11 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
     __syncwarp();
   }
   if (m != 13 || by_norm) return;
+  // ||X||_1 <= theta_13 needs no squaring: alpha <= ||X||_1 (d_p <= ||X||_1 by
+  // submultiplicativity) gives s0 = 0, and ||(|X|)^27||_1 <= ||X||_1^27 bounds
+  // the ell term by |c27| ||X||_1^26 <= 2^-53 for ||X||_1 <= 5.43 > theta_13,
+  // so ell = 0.  Only larger norms need the powers' norms and the ell estimate.
+  if (f32dec ? nrmf <= float(THETA13) : nrm <= THETA13) return;
   // log2 d_p = log2 ||X^p|| / p, p = 1..6, with X^3 = X^2 X (into T) and
   // X^5 = X^4 X (into the R2 buffer, free at this point).  Only the exponent
   // of alpha matters, so the arithmetic is FP32 (the estimate is inflated by
@@ -612,7 +710,7 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
     for (int p = 2; p <= 6; ++p) cs[p] = fmaxf(cs[p], __shfl_xor_sync(FULL, cs[p], o));
   }
   float lg[7];
-  lg[1] = log2f(float(nrm));
+  lg[1] = log2f(sizeof(PT) == 4 ? nrmf : float(nrm));
 #pragma unroll
   for (int p = 2; p <= 6; ++p) lg[p] = log2f(cs[p]) / float(p);
   float la = lg[1];  // log2 alpha = min_p max(lg_p, lg_{p+1})
@@ -636,7 +734,7 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
   float* Y2 = reinterpret_cast<float*>(A5);
   float* Y4 = reinterpret_cast<float*>(w.R1);
   {
-    const float sc = float(1.0 / nrm);
+    const float sc = 1.0f / (sizeof(PT) == 4 ? nrmf : float(nrm));
 #pragma unroll
     for (int q = 0; q < NF; ++q)
       if (LF.ok[q]) Y[LF.i[q] * LMF + LF.j[q]] = approx_abs_f32(X[LF.i[q] * LM + LF.j[q]]) * sc;
@@ -679,8 +777,18 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
   if (!(ell > 0)) ell = 0;
   s = s0 + ell;
   if (s > 0) {
-    const PT c1 = PT(ldexp(1.0, -s)), c2 = PT(ldexp(1.0, -2 * s)), c4 = PT(ldexp(1.0, -4 * s)),
-             c6 = PT(ldexp(1.0, -6 * s));
+    PT c1, c2, c4, c6;
+    if constexpr (sizeof(PT) == 4) {
+      c1 = ldexpf(1.0f, -s);
+      c2 = ldexpf(1.0f, -2 * s);
+      c4 = ldexpf(1.0f, -4 * s);
+      c6 = ldexpf(1.0f, -6 * s);
+    } else {
+      c1 = ldexp(1.0, -s);
+      c2 = ldexp(1.0, -2 * s);
+      c4 = ldexp(1.0, -4 * s);
+      c6 = ldexp(1.0, -6 * s);
+    }
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       if (L.ok[q]) {
@@ -701,7 +809,8 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
 // a_out receive the Pade degree, the squarings and the full squarings.
 template <int D, typename PT>
 __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* rows, int nrows, bool full,
-                                       double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr) {
+                                       double* E, int lde, int* m_out, int* s_out, int* a_out = nullptr,
+                                       const Asm* as = nullptr) {
   constexpr int S = Slots<D>::S;
   constexpr int NL = Lay<D, PT>::N;
   constexpr int LM = Lay<D, PT>::LDM;
@@ -710,32 +819,65 @@ __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* row
   constexpr bool F32 = sizeof(PT) == 4;
   // ||X||_1 picks the Pade degree.  The FP32 form estimates it in FP32 and
   // falls back to the FP64 sum only next to a threshold, where the estimate
-  // (relative error < 2^-16) could pick another degree.
-  double nrm;
+  // (relative error below 1e-5) could pick another degree.  With an
+  // assembly descriptor the FP32 form builds X in FP32 directly and the FP64
+  // matrix only for that fallback.
+  PT* X = w.M(0);
+  double nrm = 0.0;
+  float nrmf = 0.0f;
+  bool exact64 = !F32;
   if (F32) {
+    if (as) {
+      const float* Df = as->Dhf;
+#pragma unroll
+      for (int t = 0; t < NL; ++t) {
+        if (L.ok[t]) {
+          const int i = L.i[t], j = L.j[t];
+          float x = 0.0f;
+          if (i < as->n && j < as->n) {
+            const int o = i * LD + j;
+            x = as->c1f * Df[o];
+            x = fmaf(as->c2f, Df[DMAX * LD + o], x);
+            x = fmaf(as->c3f, Df[2 * DMAX * LD + o], x);
+            if (i == j) x += as->cIf;
+          }
+          X[i * LM + j] = PT(x);
+        }
+      }
+      __syncwarp();
+    }
     float cs = 0.0f;
     if (lane < D) {
 #pragma unroll
-      for (int i = 0; i < D; ++i) cs += approx_abs_f32(w.X64[i * LD + lane]);
+      for (int i = 0; i < D; ++i) cs += as ? fabsf(float(X[i * LM + lane])) : approx_abs_f32(w.X64[i * LD + lane]);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) cs = fmaxf(cs, __shfl_xor_sync(FULL, cs, o));
-    nrm = double(cs);
-    const double th[6] = {THETA3, THETA5, THETA7, THETA9, THETA13, 8192.0};
+    nrmf = cs;
+    const float th[6] = {float(THETA3), float(THETA5), float(THETA7), float(THETA9), float(THETA13), 8192.0f};
     bool near = !(cs > 0.0f) || !(cs < 3.0e38f);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) near |= fabs(nrm - th[q]) <= 1e-4 * th[q];
-    if (near) nrm = norm1_smem<D>(w.X64, lane);
+    for (int q = 0; q < 6; ++q) near |= fabsf(cs - th[q]) <= 1e-4f * th[q];
+    if (near) {
+      if (as) {
+        assemble64<D>(w.X64, *as, lane);
+        __syncwarp();
+      }
+      nrm = norm1_smem<D>(w.X64, lane);
+      nrmf = float(nrm);
+      exact64 = true;
+    }
   } else {
     nrm = norm1_smem<D>(w.X64, lane);
   }
-  PT* X = w.M(0);
+  if (!(F32 && as)) {
 #pragma unroll
-  for (int t = 0; t < NL; ++t)
-    if (L.ok[t]) X[L.i[t] * LM + L.j[t]] = PT(w.X64[L.i[t] * LD + L.j[t]]);
+    for (int t = 0; t < NL; ++t)
+      if (L.ok[t]) X[L.i[t] * LM + L.j[t]] = PT(w.X64[L.i[t] * LD + L.j[t]]);
+  }
   __syncwarp();
   int m, s;
-  powers_and_scaling<D, PT>(w, L, lane, nrm, m, s);
+  powers_and_scaling<D, PT>(w, L, lane, nrm, nrmf, exact64, m, s);
   PT U[NL], V[NL];
   pade_uv<D, PT>(w, m, L, U, V);
   int a = s;
@@ -747,7 +889,14 @@ __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* row
 #pragma unroll
     for (int t = 0; t < NL; ++t) {
       if (L.ok[t]) {
-        const double u = double(U[t]), v = double(V[t]);
+        double u, v;
+        if constexpr (F32) {
+          u = f2d_bits(U[t]);
+          v = f2d_bits(V[t]);
+        } else {
+          u = U[t];
+          v = V[t];
+        }
         w.G[L.j[t] * LDG + L.i[t]] = v - u;
         if (F32) Pm[L.i[t] * LM + L.j[t]] = V[t] + U[t];
         else w.R1[L.i[t] * LD + L.j[t]] = v + u;
@@ -755,7 +904,7 @@ __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* row
     }
     if (lane < D) w.G[lane * LDG + D] = lane == rows[0] ? 1.0 : 0.0;
     __syncwarp();
-    gauss_jordan<D, F32 ? 1 : 2>(w.G, lane, D + 1);
+    gauss_jordan<D, F32 ? 1 : 2, D + 1>(w.G, lane);
     if (F32) {
       float* ys = reinterpret_cast<float*>(w.V) + 2 * DMAX;
       if (lane < D) ys[lane] = float(w.G[lane * LDG + D]);
@@ -787,13 +936,20 @@ __device__ __noinline__ void warp_expm(const Ws<PT>& w, int lane, const int* row
 #pragma unroll
     for (int t = 0; t < NL; ++t) {
       if (L.ok[t]) {
-        const double u = double(U[t]), v = double(V[t]);
+        double u, v;
+        if constexpr (F32) {
+          u = f2d_bits(U[t]);
+          v = f2d_bits(V[t]);
+        } else {
+          u = U[t];
+          v = V[t];
+        }
         w.G[L.i[t] * LDG + L.j[t]] = v - u;
         w.G[L.i[t] * LDG + D + L.j[t]] = v + u;
       }
     }
     __syncwarp();
-    gauss_jordan<D>(w.G, lane);
+    gauss_jordan<D, 2, 2 * D>(w.G, lane);
     // squaring phase in FP64: R = G[:, D:2D] copied to R1, full squarings
     // ping-pong between R1 and R2, then the remaining 2^b factors act on the
     // harvested rows only.

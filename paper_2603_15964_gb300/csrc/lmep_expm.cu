@@ -8,6 +8,7 @@
 // never reach HBM.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "lmep_warp_kernel.cuh"
 
@@ -24,6 +25,71 @@ DeviceInfo device_info() {
     dev_cached = dev;
   }
   return info;
+}
+
+// ------------------------------------------------------------------ (a2) tables
+// h^k D^(k) (k = 1..3) of the uniform window depend only on n: they are built
+// once per device by Fornberg's recursion into these tables (slot (n - 3) / 2,
+// FP64 and an FP32 copy); the expm kernels copy their n's table into shared
+// memory instead of rebuilding it in every CTA.
+constexpr int FB_SLOTS = (DMAX - 1) / 2;  // n = 3, 5, ..., 15
+__device__ double g_fornberg[FB_SLOTS][3 * DMAX * LD];
+__device__ float g_fornberg_f[FB_SLOTS][3 * DMAX * LD];
+
+__global__ void k_fornberg_tables() {
+  const int n = 3 + 2 * int(blockIdx.x);
+  const int t = threadIdx.x;
+  if (t < n) {
+    double c[4][DMAX];
+    fornberg_row(double(t), n, c);
+    for (int k = 1; k <= 3; ++k)
+      for (int j = 0; j < DMAX; ++j) {
+        const double v = j < n ? c[k][j] : 0.0;
+        g_fornberg[blockIdx.x][(k - 1) * DMAX * LD + t * LD + j] = v;
+        g_fornberg_f[blockIdx.x][(k - 1) * DMAX * LD + t * LD + j] = float(v);
+      }
+  }
+}
+
+namespace {
+std::mutex g_fb_mutex;
+struct FbState {
+  bool ready = false;
+  double* d = nullptr;
+  float* f = nullptr;
+};
+FbState g_fb[64];
+}  // namespace
+
+cudaError_t fornberg_init() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_fb_mutex);
+  FbState& st = g_fb[dev];
+  if (st.ready) return cudaSuccess;
+  if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&st.d), g_fornberg)) != cudaSuccess) return e;
+  if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&st.f), g_fornberg_f)) != cudaSuccess) return e;
+  cudaStream_t s;
+  if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  k_fornberg_tables<<<FB_SLOTS, 32, 0, s>>>();
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e == cudaSuccess) st.ready = true;
+  return e;
+}
+
+static cudaError_t fornberg_of(int n, const double** d, const float** f) {
+  cudaError_t e = fornberg_init();
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int slot = (n - 3) / 2;
+  *d = g_fb[dev].d + size_t(slot) * 3 * DMAX * LD;
+  *f = g_fb[dev].f + size_t(slot) * 3 * DMAX * LD;
+  return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ (a1)-(a3)
@@ -128,6 +194,8 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
   WarpJob job{};
   job.mode = MODE_CONST;
   job.p = p;
+  cudaError_t e = fornberg_of(p.n, &job.dh, &job.dhf);
+  if (e != cudaSuccess) return e;
   job.items = B * p.n;
   job.h_inst = h_inst;
   job.out = W;
@@ -140,6 +208,8 @@ cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused
   WarpJob job{};
   job.mode = fused ? MODE_FROZEN_STEP : MODE_FROZEN_W;
   job.p = p;
+  cudaError_t e = fornberg_of(p.n, &job.dh, &job.dhf);
+  if (e != cudaSuccess) return e;
   job.items = p.N * (p.batch > 1 ? p.batch : 1);
   job.u = u;
   job.out = out;

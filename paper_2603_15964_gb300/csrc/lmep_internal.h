@@ -19,8 +19,10 @@ struct KParams {
   int n_phi;
   double bc_lo, bc_hi;
   double dt, c0, c1, c2, c3, fa;
-  // derived on the host once per launch: dt/h, dt c0, dt c2/h^2, dt c3/h^3
+  // derived on the host once per launch: dt/h, dt c0, dt c2/h^2, dt c3/h^3,
+  // and their FP32 roundings for the FP32 form
   double dt_h, c0dt, c2h, c3h;
+  float c0dt_f, c2h_f, c3h_f;
 };
 
 // Set the thread-local text returned by lmep_last_error().
@@ -33,6 +35,8 @@ struct DeviceInfo {
 DeviceInfo device_info();
 
 // ---- expm family (lmep_expm.cu)
+// Build the per-n derivative tables on the current device (once; synchronous).
+cudaError_t fornberg_init();
 cudaError_t launch_build_operator(const KParams& p, const double* u, int64_t i0, int64_t count,
                                   double* M, int32_t* start, int32_t* row, cudaStream_t s);
 cudaError_t launch_expm(const double* A, int64_t P, int d, double* E, bool mixed, int32_t* ms,

@@ -23,6 +23,9 @@
 namespace lmep {
 
 constexpr int DH_BYTES = 3 * DMAX * LD * 8;  // h^k D^(k), k = 1..3
+constexpr int DHF_BYTES = 3 * DMAX * LD * 4;  // their FP32 copy (FP32 form)
+template <typename PT>
+constexpr int dh_bytes() { return DH_BYTES + (sizeof(PT) == 4 ? DHF_BYTES : 0); }
 constexpr int WARPS = 4;                      // warps per CTA
 
 enum { MODE_FULL = 0, MODE_CONST = 1, MODE_FROZEN_W = 2, MODE_FROZEN_STEP = 3 };
@@ -38,6 +41,8 @@ struct WarpJob {
   const void* u;        // frozen velocities / state
   void* out;            // weights or next state
   unsigned* flags;
+  const double* dh;     // h^k D^(k) tables of this n (device, FP64 and FP32), not MODE_FULL
+  const float* dhf;
 };
 
 // X = cI I + c1h Dh1 + c2h Dh2 + c3h Dh3 on the n x n window, zero-padded to D.
@@ -78,12 +83,19 @@ template <int D, typename PT>
 __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob job) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
+  float* Dhf = sizeof(PT) == 4 ? reinterpret_cast<float*>(smem + DH_BYTES) : nullptr;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Ws<PT> w(smem + DH_BYTES + warp * Ws<PT>::BYTES);
+  Ws<PT> w(smem + dh_bytes<PT>() + warp * Ws<PT>::BYTES);
   const KParams& p = job.p;
   const int mode = job.mode;
   const int n = p.n;
-  if (mode != MODE_FULL) fornberg_block(Dh, n);
+  if (mode != MODE_FULL) {
+    // copy the window's derivative tables (built once per device)
+    for (int e = threadIdx.x; e < 3 * DMAX * LD; e += blockDim.x) {
+      Dh[e] = job.dh[e];
+      if (Dhf) Dhf[e] = job.dhf[e];
+    }
+  }
   __syncthreads();
   using ST = PT;
   const ST* u = static_cast<const ST*>(job.u);
@@ -104,8 +116,9 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       continue;
     }
     if (mode == MODE_CONST) {
-      const int64_t b = it / n;
-      const int r = int(it - b * n);
+      int64_t b, rr;
+      split_index(it, n, 2, b, rr);
+      const int r = int(rr);
       const double h = job.h_inst ? job.h_inst[b] : p.h;
       const int q1 = 1 + p.n_phi;
       int rows[4];
@@ -132,8 +145,8 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       continue;
     }
     // frozen velocity: point i of instance b (instances of N points back to back)
-    const int64_t b = it / p.N;
-    const int64_t i = it - b * p.N;
+    int64_t b, i;
+    split_index(it, p.N, p.batch, b, i);
     const ST* ub = u + b * p.N;
     if (dir && (i == 0 || i == p.N - 1)) {  // walls keep their values; no weights
       if (out) {
@@ -151,14 +164,20 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
     const int r = int(i - st);
     const double a1 = p.c1 - p.fa * ui;
     const int kr = recentring_shift(a1, p.dt_h, n, r);
-    assemble<D>(w.X64, Dh, n, p.c0dt, fma(a1, p.dt_h, double(kr)), p.c2h, p.c3h, lane);
-    __syncwarp();
+    const double c1h = fma(a1, p.dt_h, double(kr));
+    Asm as{Dh, Dhf, n, p.c0dt, c1h, p.c2h, p.c3h, p.c0dt_f, 0.0f, p.c2h_f, p.c3h_f};
+    if (sizeof(PT) == 4) {
+      as.c1f = __double2float_rn(c1h);  // X is assembled in FP32 inside warp_expm
+    } else {
+      assemble<D>(w.X64, Dh, n, p.c0dt, c1h, p.c2h, p.c3h, lane);
+      __syncwarp();
+    }
     const int hr = r - kr;
     // the window values are loaded now so that their latency hides behind the expm
     ST uw = ST(0);
     if (mode == MODE_FROZEN_STEP && lane < n) uw = ub[grid_index(st + lane, p.N, p.bc)];
     int m_, s_, a_;
-    warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, &m_, &s_, &a_);
+    warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, &m_, &s_, &a_, sizeof(PT) == 4 ? &as : nullptr);
     if (job.ms && lane == 0) {
       job.ms[3 * it] = m_;
       job.ms[3 * it + 1] = s_;
@@ -174,7 +193,7 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       acc = warp_sum(acc);
       if (lane == 0) {
         out[it] = acc;
-        bad |= !isfinite(double(acc));
+        bad |= !isfinite(acc);
       }
     } else {
       if (lane < n) out[it * n + lane] = ST(w.V[lane]);
@@ -186,7 +205,7 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
 
 template <int D, typename PT>
 cudaError_t run_warp(const WarpJob& job, cudaStream_t s) {
-  const size_t smem = DH_BYTES + WARPS * Ws<PT>::BYTES;
+  const size_t smem = dh_bytes<PT>() + WARPS * Ws<PT>::BYTES;
   auto k = k_warp<D, PT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;

@@ -48,3 +48,15 @@ def test_pade_recurrence_matches_closed_form():
             closed = Fraction(math.factorial(2 * m - j - 1) * math.factorial(m),
                               math.factorial(2 * m) * math.factorial(j + 1) * math.factorial(m - j - 1))
             assert b == closed
+
+
+def test_no_ell_correction_below_theta13():
+    """The kernel skips the 2009 ell estimate when ||X||_1 <= theta_13.  That is
+    exact because ||(|X|)^27||_1 / ||X||_1 <= ||X||_1^26, so the ell argument
+    |c27| ||X||_1^26 stays below u = 2^-53 up to ||X||_1 = 5.43 > theta_13."""
+    th = float(re.search(r"THETA13 = ([0-9.e+-]+);", source()).group(1))
+    c27 = Fraction(math.factorial(13) ** 2, math.factorial(26) * math.factorial(27))
+    bound = math.log2(c27) + 26 * math.log2(th)
+    assert bound < -53
+    limit = 2 ** ((-53 - math.log2(c27)) / 26)
+    assert 5.42 < limit < 5.44 and th < limit
