@@ -606,6 +606,16 @@ __device__ __forceinline__ float approx_abs_f32(double x) {
   return __int_as_float((e << 23) | ((hi & 0xfffff) << 3));
 }
 __device__ __forceinline__ float approx_abs_f32(float x) { return fabsf(x); }
+// x as a float with integer operations only (mantissa truncated to 20 bits,
+// relative error < 2^-20; underflow to zero, overflow to Inf).  For estimates.
+__device__ __forceinline__ float approx_f32(double x) {
+  const int hi = __double2hiint(x);
+  const int sg = hi & int(0x80000000);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __int_as_float(sg);
+  if (e >= 255) return __int_as_float(sg | 0x7f800000);
+  return __int_as_float(sg | (e << 23) | ((hi & 0xfffff) << 3));
+}
 
 // 1-norm (max column sum) of a D x D matrix in shared memory, all lanes.
 template <int D, typename T>
@@ -687,21 +697,61 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
   // 2^-12 to stay an upper bound); the six column-sum maxima are reduced
   // together.
   PT* A5 = reinterpret_cast<PT*>(w.R2);
-  L.mm(A2, X, acc);
-  lay_store<D>(L, T, acc);
-  L.mm(A4, X, acc);
-  lay_store<D>(L, A5, acc);
-  __syncwarp();
   float cs[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (lane < D) {
+  if constexpr (sizeof(PT) == 8) {
+    // FP64 path: the two odd powers only feed these norm estimates, so they
+    // are formed in FP32 from FP32 copies of X, X^2 and X^4 (slot 4 and R2,
+    // which are contiguous, hold the copies; R1 holds X^3; X^5 overwrites the
+    // X^2 copy) and the FP64 pipe is spared two products.
+    static_assert(Ws<double>::R2_OFF == Ws<double>::PRD_OFF + 5 * DMAX * LD * 8, "slot 4 and R2 adjoin");
+    const Lay<D, float> LQ(lane);
+    constexpr int LQM = Lay<D, float>::LDM;
+    constexpr int NQ = Lay<D, float>::N;
+    float* Xf = reinterpret_cast<float*>(T);
+    float* A2f = Xf + DMAX * LQM;
+    float* A4f = A2f + DMAX * LQM;
+    float* A3f = reinterpret_cast<float*>(w.R1);
+    for (int e = lane; e < D * D; e += 32) {
+      const int i = e / D, j = e - (e / D) * D;
+      Xf[i * LQM + j] = approx_f32(X[i * LM + j]);
+      A2f[i * LQM + j] = approx_f32(A2[i * LM + j]);
+      A4f[i * LQM + j] = approx_f32(A4[i * LM + j]);
+    }
+    __syncwarp();
+    float q[NQ];
+    LQ.mm(A2f, Xf, q);
+    lay_store<D>(LQ, A3f, q);
+    LQ.mm(A4f, Xf, q);
+    __syncwarp();
+    lay_store<D>(LQ, A2f, q);  // X^5
+    __syncwarp();
+    if (lane < D) {
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-      const int o = i * LM + lane;
-      cs[2] += approx_abs_f32(A2[o]);
-      cs[3] += approx_abs_f32(T[o]);
-      cs[4] += approx_abs_f32(A4[o]);
-      cs[5] += approx_abs_f32(A5[o]);
-      cs[6] += approx_abs_f32(A6[o]);
+      for (int i = 0; i < D; ++i) {
+        const int o = i * LM + lane, of = i * LQM + lane;
+        cs[2] += approx_abs_f32(A2[o]);
+        cs[3] += fabsf(A3f[of]);
+        cs[4] += approx_abs_f32(A4[o]);
+        cs[5] += fabsf(A2f[of]);
+        cs[6] += approx_abs_f32(A6[o]);
+      }
+    }
+  } else {
+    L.mm(A2, X, acc);
+    lay_store<D>(L, T, acc);
+    L.mm(A4, X, acc);
+    lay_store<D>(L, A5, acc);
+    __syncwarp();
+    if (lane < D) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const int o = i * LM + lane;
+        cs[2] += approx_abs_f32(A2[o]);
+        cs[3] += approx_abs_f32(T[o]);
+        cs[4] += approx_abs_f32(A4[o]);
+        cs[5] += approx_abs_f32(A5[o]);
+        cs[6] += approx_abs_f32(A6[o]);
+      }
     }
   }
 #pragma unroll
