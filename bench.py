@@ -521,6 +521,197 @@ def allen_cahn_config(B, batch):
             "l2": "state (254 MB FP32) larger than L2; no flush"}
 
 
+# ------------------------------------------------------------------ adjoint (a7)
+ADJ_N = 262144
+ADJ_NS = 9
+ADJ_CFL = 2.0
+
+
+def adj_problem(steps: int, seed: int = 0):
+    import workloads as wl
+    return wl.burgers(N=ADJ_N, n=ADJ_NS, cfl=ADJ_CFL, nu=NU, steps=steps, seed=seed, departure_centring=True)
+
+
+def adj_flops(n: int, s):
+    """FP64 FLOPs of one reverse point step of the adjoint kernel with s squarings: 32 + 5 s
+    n x n products (powers, the two Frechet directions, U, V and their derivatives, the two
+    L = Y1 + Y2 R), the Gauss-Jordan solve of [Q | P | 4 derivative blocks] (6 n^3 FMAs) and
+    the two dot products of the harvested rows."""
+    import numpy as np
+    return float(np.sum(2.0 * n ** 3 * (32 + 5 * s) + 12.0 * n ** 3 + 4.0 * n))
+
+
+def _oracle_grad(task):
+    """Oracle gradient of one instance (initial state seed `seed`) of the batch whose common dt comes
+    from the seed-0 initial state, as on the GPU."""
+    n_pts, steps, seed = task
+    import workloads as wl
+    from oracle import adjoint as oadj
+    p = wl.burgers(N=n_pts, n=ADJ_NS, cfl=ADJ_CFL, nu=NU, steps=steps, seed=0, departure_centring=True)
+    return oadj.gradient(p, wl.burgers_ic(n_pts, seed), wl.burgers_ic(n_pts, 1000 + seed), steps)
+
+
+def adjoint_config(B, K):
+    return {"workload": f"adjoint of frozen-velocity viscous Burgers (config 5 shape): Dirichlet u=0 on [-1,1], "
+                        f"N={ADJ_N}, {B} instances in one launch (seeds 0..{B - 1}), n={ADJ_NS}, CFL={ADJ_CFL}, "
+                        f"nu={NU}, departure-centred; J = h/2 sum_b ||u_b(T) - u*_b||^2 (targets seeds 1000+b); "
+                        f"{K} forward steps (FP32 form, checkpoint every 2) + the reverse sweep (FP64 Frechet "
+                        "derivatives, FP32 lambda) through torch.autograd",
+            "points_per_step": ADJ_N * B, "unit_note": "a step = one forward point-update + its reverse step"}
+
+
+def adjoint_main(args, rank, world, local_rank, cores):
+    import numpy as np
+    B, K = max(1, args.adj_batch), max(1, args.adj_steps)
+    pool = None
+    if rank == 0 and world == 1:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(cores, 4))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        npts = 0
+        for k in range(args.steps):
+            pool.map(_oracle_grad, [(256, 1, k * 4 + q) for q in range(min(cores, 4))])
+            npts += 256 * min(cores, 4)
+        dt = time.perf_counter() - t0
+        pool.close()
+        v = npts / dt
+        line = {"impl": "reference", "metric": "gradient point-steps/s (forward + reverse)", "value": v,
+                "unit": "point-steps/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": adjoint_config(B, K),
+                "cpu_baseline": {"value": v, "unit": "point-steps/s", "cores": min(cores, 4), "kind": "oracle",
+                                 "sample": "one step of the oracle gradient of 4 instances of N = 256 per step"},
+                "e2e": {"value": v, "unit": "point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    import workloads as wl
+    from paper_2603_15964_gb300.autograd import FrozenVelocitySolver
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = adj_problem(K)
+    u0 = np.stack([wl.burgers_ic(ADJ_N, rank * B + b) for b in range(B)]).astype(np.float32)
+    tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + rank * B + b) for b in range(B)]),
+                       dtype=torch.float32, device=dev)
+    solver = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="mixed", checkpoint_every=2)
+    x0 = torch.tensor(u0, device=dev)
+
+    def grad_once(x_init):
+        x = x_init.clone().requires_grad_(True)
+        nu = torch.tensor(p.c2, dtype=torch.float64, requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        uT = solver(x, nu)
+        J = 0.5 * p.h * ((uT - tgt) ** 2).sum()
+        e1.record()
+        J.backward()
+        e2.record()
+        e2.synchronize()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), x.grad, nu.grad
+
+    for _ in range(max(1, args.warmup // 3)):
+        grad_once(x0)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    t_fwd, t_bwd, g, gnu = grad_once(x0)
+    clk = clocks.stop()
+    L.lmep_sync_status(solver.handle)
+    total = t_fwd + t_bwd
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = float(t.item())
+    pts = ADJ_N * B * K * world
+    # roofline of the adjoint kernel: launches timed alone on the initial states
+    grid = solver.grid(B)
+    op = solver.op(p.c2)
+    lam_next = torch.ones_like(x0)
+    lam = torch.empty_like(x0)
+    dnu = torch.zeros(1, dtype=torch.float64, device=dev)
+    scratch = torch.empty(L.lmep_adjoint_scratch_bytes(grid, "mixed"), dtype=torch.uint8, device=dev)
+    stats = torch.zeros(ADJ_N * B, 3, dtype=torch.int32, device=dev)
+    L.lmep_frozen_stats(solver.handle, grid, op, p.dt, x0, stats, "mixed")
+    s_pts = stats[:, 1].cpu().numpy()
+    L.lmep_adjoint_step(solver.handle, grid, op, p.dt, x0, lam_next, lam, dnu, scratch, "mixed")
+    ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    ka.record()
+    for _ in range(reps):
+        L.lmep_adjoint_step(solver.handle, grid, op, p.dt, x0, lam_next, lam, dnu, scratch, "mixed")
+    kb.record()
+    kb.synchronize()
+    adj_ms = ka.elapsed_time(kb) / reps
+    flops = adj_flops(ADJ_NS, s_pts)
+    achieved = flops / (adj_ms * 1e-3)
+    # e2e: host initial states in (pinned), gradient back to the host
+    host_u0 = torch.tensor(u0).pin_memory()
+    host_g = torch.empty_like(host_u0).pin_memory()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record()
+    xd = host_u0.to(dev, non_blocking=True)
+    _, _, gg, _ = grad_once(xd)
+    host_g.copy_(gg, non_blocking=True)
+    eb.record()
+    eb.synchronize()
+    e2e_ms = ea.elapsed_time(eb)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    cpu = err = None
+    if pool is not None:
+        q = min(cores, 4)
+        t0 = time.perf_counter()
+        outs = pool.map(_oracle_grad, [(4096, 1, b) for b in range(q)])
+        dt = time.perf_counter() - t0
+        pool.close()
+        cpu = {"value": 4096 * q / dt, "unit": "point-steps/s", "cores": q, "kind": "oracle",
+               "sample": f"oracle gradient, one step, {q} instances of N = 4096 (same n, CFL, nu), {dt:.1f} s"}
+        # stated error: the GPU gradient of the same reduced problem against the oracle's
+        pr = wl.burgers(N=4096, n=ADJ_NS, cfl=ADJ_CFL, nu=NU, steps=1, seed=0, departure_centring=True)
+        sr = FrozenVelocitySolver(N=4096, h=pr.h, n=pr.n, dt=pr.dt, steps=1, precision="mixed", checkpoint_every=1)
+        xr = torch.tensor(np.stack([wl.burgers_ic(4096, b) for b in range(q)]).astype(np.float32), device=dev,
+                          requires_grad=True)
+        nur = torch.tensor(pr.c2, dtype=torch.float64, requires_grad=True)
+        tr = torch.tensor(np.stack([wl.burgers_ic(4096, 1000 + b) for b in range(q)]), device=dev)
+        Jr = 0.5 * pr.h * ((sr(xr, nur).double() - tr) ** 2).sum()
+        Jr.backward()
+        gu = xr.grad.double().cpu().numpy()
+        want_u = np.stack([o[1] for o in outs])
+        want_nu = sum(o[2] for o in outs)
+        err = {"grad_u_rel_linf": float(np.max(np.abs(gu - want_u)) / np.max(np.abs(want_u))),
+               "grad_nu_rel": float(abs(float(nur.grad) - want_nu) / abs(want_nu)),
+               "note": "FP32 form forward, FP32 initial state rounding included"}
+    line = {"metric": "gradient point-steps/s (forward + reverse)", "value": pts / (total * 1e-3),
+            "unit": "point-steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 forward + f64 Frechet", "data": "synthetic", "config": adjoint_config(B, K),
+            "forward_ms": t_fwd, "reverse_ms": t_bwd,
+            "error": {"vs": "FP64 oracle gradient, one step, 4 instances of N = 4096", "rel": err},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
+                         "unit": "TFLOP/s", "frac": achieved / P64_NOMINAL, "traffic": None,
+                         "kernel": f"k_adjoint_points<{ADJ_NS}> + k_adjoint_gather (one reverse step, {B} instances)",
+                         "avg_launch_ms": adj_ms, "flops_per_launch": flops,
+                         "note": "FP64 FLOPs of adj_flops per launch / CUDA-event time; peak = GB300 nominal FP64"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "point-steps/s",
+                    "h2d_bytes_per_step": 4 * ADJ_N * B, "d2h_bytes_per_step": 4 * ADJ_N * B},
+            # forward K frozen steps, the recomputed steps of each 2-step segment, two kernels per
+            # reverse step
+            "gpu_launches": K + (K - (K + 1) // 2) + 2 * K, "clocks": clk,
+            "gradient_nu": float(gnu)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,9 +722,12 @@ def main():
                     help="oracle points per instance for cpu_baseline (0: every interior point of the step)")
     ap.add_argument("--cpu-points", type=float, default=12e6,
                     help="Allen-Cahn cpu_baseline: oracle point-updates (whole instances in batch order)")
-    ap.add_argument("--workload", choices=["burgers", "allen_cahn"], default="burgers",
-                    help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply")
+    ap.add_argument("--workload", choices=["burgers", "allen_cahn", "adjoint"], default="burgers",
+                    help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply; "
+                         "adjoint: forward + reverse sweep of the frozen-velocity step (gradient)")
     ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
+    ap.add_argument("--adj-batch", type=int, default=8, help="adjoint workload: Burgers instances per launch")
+    ap.add_argument("--adj-steps", type=int, default=4, help="adjoint workload: forward + reverse steps timed")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -543,6 +737,8 @@ def main():
     cores = os.cpu_count() or 1
     if args.workload == "allen_cahn":
         return allen_cahn_main(args, rank, world, local_rank, cores)
+    if args.workload == "adjoint":
+        return adjoint_main(args, rank, world, local_rank, cores)
 
     if args.impl == "reference":
         if rank != 0:

@@ -150,6 +150,12 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
   double dnu_acc = 0.0;
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
   for (int64_t it = int64_t(blockIdx.x) * AW + warp; it < items; it += int64_t(gridDim.x) * AW) {
+    // the squaring phase swaps these scratch roles in place: every point starts from the same layout
+    T = Mt(7);
+    for (int q = 0; q < 2; ++q) {
+      LU[q] = Mt(16 + q);
+      LV[q] = Mt(18 + q);
+    }
     int64_t bb, i;
     split_index(it, p.N, p.batch, bb, i);
     const ST* ub = u + bb * p.N;

@@ -5,6 +5,11 @@ fused frozen-velocity Burgers step (N = 65536, n = 13, CFL = 4, nu = 1e-6,
 departure-centred) in the FP32 form and one in FP64.  Used with
 `ncu -k regex:k_warp -s 4 -c 2` (the two launches after four warm-up launches).
 
+`python -m paper_2603_15964_gb300.profile_case adj`: one reverse step of the
+frozen-velocity Burgers adjoint (N = 262144, one instance, n = 9, CFL = 2,
+FP32 state, FP64 Frechet derivatives) after one warm-up step.  Used with
+`ncu -k regex:k_adjoint_points -s 1 -c 1`.
+
 `python -m paper_2603_15964_gb300.profile_case ac [tile block]`: the batched
 Allen-Cahn ETDRK2 step (4096 instances, N log-uniform in [1024, 65536],
 n = 9, FP32 state, 254 MB): three warm-up steps, then one step.  Used with
@@ -59,8 +64,32 @@ def allen_cahn(tile: int = 1024, block: int = 128) -> None:
     print("profile case ok")
 
 
+def adjoint() -> None:
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    import workloads as wl
+
+    p = wl.burgers(N=262144, n=9, cfl=2.0, nu=1e-6, steps=1)
+    g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True)
+    op = L.Operator(c2=p.c2, frozen_adv=1.0)
+    h = L.Handle()
+    u = torch.tensor(wl.burgers_ic(p.N, 0), dtype=torch.float32, device="cuda")
+    lam_next = torch.ones_like(u)
+    lam = torch.empty_like(u)
+    dnu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    scratch = torch.empty(L.lmep_adjoint_scratch_bytes(g, "mixed"), dtype=torch.uint8, device="cuda")
+    for _ in range(2):                                    # one warm-up step, then the profiled one
+        L.lmep_adjoint_step(h, g, op, p.dt, u, lam_next, lam, dnu, scratch, "mixed")
+    L.lmep_sync_status(h)
+    torch.cuda.synchronize()
+    print("profile case ok")
+
+
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "ac":
+    if len(sys.argv) > 1 and sys.argv[1] == "adj":
+        adjoint()
+    elif len(sys.argv) > 1 and sys.argv[1] == "ac":
         allen_cahn(*(int(a) for a in sys.argv[2:]))
     else:
         main(*(float(a) if i else int(a) for i, a in enumerate(sys.argv[1:])))

@@ -101,3 +101,30 @@ def test_gradient_matches_central_differences_of_the_gpu_forward(L):
     e = 1e-3 * p.c2
     fd_nu = (J_of(u0, p.c2 + e) - J_of(u0, p.c2 - e)) / (2 * e)
     assert abs(fd_nu - gnu) <= 1e-5 * abs(fd_nu)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,cfl,nu,N,steps", [(9, 2.0, 1e-6, 512, 2), (13, 4.0, 1e-6, 300, 1), (7, 1.0, 1e-3, 257, 3)])
+def test_gradient_matches_oracle_across_configs(L, precision, n, cfl, nu, N, steps):
+    p = wl.burgers(N=N, n=n, cfl=cfl, nu=nu, steps=steps, departure_centring=True)
+    B = 3
+    u0 = np.stack([wl.burgers_ic(p.N, 20 + b) for b in range(B)])
+    target = np.stack([wl.burgers_ic(p.N, 1020 + b) for b in range(B)])
+    if precision == "mixed":
+        u0 = u0.astype(np.float32).astype(np.float64)
+    J, gu, gnu = loss_and_grads(L, p, precision, 2, u0, target)
+    want_u = np.zeros_like(u0)
+    want_nu = 0.0
+    for b in range(B):
+        _, gb, nb = oadj.gradient(p, u0[b], target[b], p.steps)
+        want_u[b] = gb
+        want_nu += nb
+    # Sizes above 2 x 152 points make the adjoint kernel's warps loop over several points.
+    # dJ/dnu: the nu direction E = dt/h^2 Dh2 is about 1e3 times X in norm at n = 13, CFL 4;
+    # the GPU's differentiated Pade and the oracle's Frechet evaluation round differently at
+    # ~1e-9 relative per term there (the sum itself cancels only by a factor ~2), hence 1e-8.
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    tol_nu = 1e-8 if precision == "fp64" else 1e-4
+    err_u = np.max(np.abs(gu - want_u)) / np.max(np.abs(want_u))
+    err_nu = abs(gnu - want_nu) / abs(want_nu)
+    assert err_u <= tol and err_nu <= tol_nu, (err_u, err_nu, int(np.argmax(np.max(np.abs(gu - want_u), axis=0))))
