@@ -28,20 +28,29 @@ namespace lmep {
 namespace {
 
 constexpr int AW = 2;                      // warps per CTA
-constexpr int DHB = 3 * DMAX * LD * 8;     // Dh1..Dh3 bytes
-constexpr int MATB = DMAX * LD * 8;        // one d x d double matrix
+constexpr int DHB = 3 * DMAX * LD * 8;     // Dh1..Dh3 bytes (DMAX x LD layout of the tables)
 constexpr int NMAT = 20;                   // matrices per warp
-constexpr int GJB = DMAX * (6 * DMAX + 1) * 8;
-constexpr int WSB = NMAT * MATB + GJB;
+
+// Per-warp workspace sized for the window: d x d matrices with row stride
+// d + 1 and the Gauss-Jordan block [Q | 5 right-hand sides] with row stride
+// 6 d + 1, so that small stencils fit several warps per SM.
+template <int D>
+struct AdjWs {
+  static constexpr int LDA = D + 1;
+  static constexpr int MAT = D * LDA;
+  static constexpr int LDGA = 6 * D + 1;
+  static constexpr int BYTES = (NMAT * MAT + D * LDGA) * 8;
+};
 
 template <int D>
 __device__ __forceinline__ void mm(const double* A, const double* B, double* C, int lane, double beta = 0.0) {
+  constexpr int LA = AdjWs<D>::LDA;
   for (int e = lane; e < D * D; e += 32) {
     const int i = e / D, j = e - (e / D) * D;
-    double acc = beta == 0.0 ? 0.0 : beta * C[i * LD + j];
+    double acc = beta == 0.0 ? 0.0 : beta * C[i * LA + j];
 #pragma unroll
-    for (int k = 0; k < D; ++k) acc = fma(A[i * LD + k], B[k * LD + j], acc);
-    C[i * LD + j] = acc;
+    for (int k = 0; k < D; ++k) acc = fma(A[i * LA + k], B[k * LA + j], acc);
+    C[i * LA + j] = acc;
   }
   __syncwarp();
 }
@@ -51,7 +60,7 @@ template <int D>
 __device__ __forceinline__ void lc(double* C, double a0, const double* M0, double a1, const double* M1,
                                    double a2, const double* M2, double cI, int lane) {
   for (int e = lane; e < D * D; e += 32) {
-    const int i = e / D, j = e - (e / D) * D, o = i * LD + j;
+    const int i = e / D, j = e - (e / D) * D, o = i * AdjWs<D>::LDA + j;
     double x = (i == j) ? cI : 0.0;
     if (M0) x = fma(a0, M0[o], x);
     if (M1) x = fma(a1, M1[o], x);
@@ -61,13 +70,12 @@ __device__ __forceinline__ void lc(double* C, double a0, const double* M0, doubl
   __syncwarp();
 }
 
-// Gauss-Jordan with partial pivoting on G = [Q | B1 | ... | B_nb] (stride 6*DMAX+1).
+// Gauss-Jordan with partial pivoting on G = [Q | B1 | ... | B_nb] (row stride 6 D + 1,
+// the right-hand-side blocks contiguous after Q).
 template <int D>
 __device__ void gj_multi(double* G, int nb, int lane) {
-  const int ldg = 6 * DMAX + 1;
+  constexpr int ldg = AdjWs<D>::LDGA;
   const int W = D * (1 + nb);
-  auto col = [&](int c) { return c < D ? c : DMAX + (c - D) / D * DMAX + (c - D) % D; };
-  (void)col;
   for (int k = 0; k < D; ++k) {
     long long key = -1;
     int idx = k;
@@ -85,8 +93,7 @@ __device__ void gj_multi(double* G, int nb, int lane) {
       }
     }
     if (idx != k) {
-      for (int c = lane; c < W; c += 32) {
-        const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
+      for (int j = lane; j < W; j += 32) {
         const double t = G[k * ldg + j];
         G[k * ldg + j] = G[idx * ldg + j];
         G[idx * ldg + j] = t;
@@ -94,17 +101,13 @@ __device__ void gj_multi(double* G, int nb, int lane) {
     }
     __syncwarp();
     const double inv = 1.0 / G[k * ldg + k];
-    for (int c = k + 1 + lane; c < W; c += 32) {
-      const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
-      G[k * ldg + j] *= inv;
-    }
+    for (int j = k + 1 + lane; j < W; j += 32) G[k * ldg + j] *= inv;
     __syncwarp();
     const int nc = W - k - 1;
     for (int e = lane; e < (D - 1) * nc; e += 32) {
       const int ii = e / nc, cc = e - (e / nc) * nc;
       const int i = ii + (ii >= k ? 1 : 0);
-      const int c = k + 1 + cc;
-      const int j = c < D ? c : DMAX + ((c - D) / D) * DMAX + (c - D) % D;
+      const int j = k + 1 + cc;
       G[i * ldg + j] = fma(-G[i * ldg + k], G[k * ldg + j], G[i * ldg + j]);
     }
     __syncwarp();
@@ -119,8 +122,9 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* base = reinterpret_cast<double*>(smem + DHB + warp * WSB);
-  auto Mt = [&](int q) { return base + q * DMAX * LD; };
+  constexpr int LA = AdjWs<D>::LDA;
+  double* base = reinterpret_cast<double*>(smem + DHB + warp * AdjWs<D>::BYTES);
+  auto Mt = [&](int q) { return base + q * AdjWs<D>::MAT; };
   double* X = Mt(0);
   double* A2 = Mt(1);
   double* A4 = Mt(2);
@@ -135,8 +139,8 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
   double* M6[2] = {Mt(14), Mt(15)};
   double* LU[2] = {Mt(16), Mt(17)};
   double* LV[2] = {Mt(18), Mt(19)};
-  double* G = base + NMAT * DMAX * LD;
-  const int ldg = 6 * DMAX + 1;
+  double* G = base + NMAT * AdjWs<D>::MAT;
+  constexpr int ldg = AdjWs<D>::LDGA;
   __shared__ double dnu_blk;
   if (threadIdx.x == 0) dnu_blk = 0.0;
   fornberg_block(Dh, p.n);
@@ -178,19 +182,19 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     const double c1h = p.dt * a1 / p.h + double(kr);
     const double c2h = p.dt * p.c2 / (p.h * p.h), c3h = p.dt * p.c3 / (p.h * p.h * p.h);
     for (int e = lane; e < D * D; e += 32) {
-      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
-      double x = c1h * Dh[o];
-      x = fma(c2h, Dh[DMAX * LD + o], x);
-      if (c3h != 0.0) x = fma(c3h, Dh[2 * DMAX * LD + o], x);
+      const int a = e / D, b = e - (e / D) * D, od = a * LD + b, o = a * LA + b;
+      double x = c1h * Dh[od];
+      x = fma(c2h, Dh[DMAX * LD + od], x);
+      if (c3h != 0.0) x = fma(c3h, Dh[2 * DMAX * LD + od], x);
       if (a == b) x += p.dt * p.c0;
       X[o] = x;
-      E[0][o] = -(p.dt * p.fa / p.h) * Dh[o];
-      E[1][o] = (p.dt / (p.h * p.h)) * Dh[DMAX * LD + o];
+      E[0][o] = -(p.dt * p.fa / p.h) * Dh[od];
+      E[1][o] = (p.dt / (p.h * p.h)) * Dh[DMAX * LD + od];
     }
     __syncwarp();
     double cs = 0.0;
     if (lane < D)
-      for (int a = 0; a < D; ++a) cs += fabs(X[a * LD + lane]);
+      for (int a = 0; a < D; ++a) cs += fabs(X[a * LA + lane]);
     const double nrm = warp_max(cs);
     int s = 0;
     {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     }
     const double sc = ldexp(1.0, -s);
     for (int e = lane; e < D * D; e += 32) {
-      const int o = (e / D) * LD + e % D;
+      const int o = (e / D) * LA + e % D;
       X[o] *= sc;
       E[0][o] *= sc;
       E[1][o] *= sc;
@@ -239,13 +243,13 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     mm<D>(A6, Z1, W1, lane, 1.0);
     // G = [V-U | V+U | LU+LV (u) | LU-LV (u) | LU+LV (nu) | LU-LV (nu)]
     for (int e = lane; e < D * D; e += 32) {
-      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
+      const int a = e / D, b = e - (e / D) * D, o = a * LA + b;
       const double Uv = T[o], Vv = W1[o];
       G[a * ldg + b] = Vv - Uv;
-      G[a * ldg + DMAX + b] = Vv + Uv;
+      G[a * ldg + D + b] = Vv + Uv;
       for (int q = 0; q < 2; ++q) {
-        G[a * ldg + (2 + 2 * q) * DMAX + b] = LU[q][o] + LV[q][o];
-        G[a * ldg + (3 + 2 * q) * DMAX + b] = LU[q][o] - LV[q][o];
+        G[a * ldg + (2 + 2 * q) * D + b] = LU[q][o] + LV[q][o];
+        G[a * ldg + (3 + 2 * q) * D + b] = LU[q][o] - LV[q][o];
       }
     }
     __syncwarp();
@@ -253,11 +257,11 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     // R into Wm, L_q = Y1 + Y2 R into LU[q]
     double* R = Wm;
     for (int e = lane; e < D * D; e += 32) {
-      const int a = e / D, b = e - (e / D) * D, o = a * LD + b;
-      R[o] = G[a * ldg + DMAX + b];
+      const int a = e / D, b = e - (e / D) * D, o = a * LA + b;
+      R[o] = G[a * ldg + D + b];
       for (int q = 0; q < 2; ++q) {
-        LU[q][o] = G[a * ldg + (2 + 2 * q) * DMAX + b];
-        LV[q][o] = G[a * ldg + (3 + 2 * q) * DMAX + b];
+        LU[q][o] = G[a * ldg + (2 + 2 * q) * D + b];
+        LV[q][o] = G[a * ldg + (3 + 2 * q) * D + b];
       }
     }
     __syncwarp();
@@ -279,9 +283,9 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     // outputs: w = R[hr], g_q = L_q[hr] . u[window]
     double uj = 0.0;
     if (lane < n) uj = double(ub[grid_index(st + lane, p.N, p.bc)]);
-    const double gu = warp_sum(lane < n ? LU[0][hr * LD + lane] * uj : 0.0);
-    const double gn = warp_sum(lane < n ? LU[1][hr * LD + lane] * uj : 0.0);
-    if (lane < n) Wout[it * n + lane] = ST(R[hr * LD + lane]);
+    const double gu = warp_sum(lane < n ? LU[0][hr * LA + lane] * uj : 0.0);
+    const double gn = warp_sum(lane < n ? LU[1][hr * LA + lane] * uj : 0.0);
+    if (lane < n) Wout[it * n + lane] = ST(R[hr * LA + lane]);
     if (lane == 0) {
       gu_out[it] = ST(gu);
       st_out[it] = int32_t(st - i);
@@ -333,7 +337,7 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
   ST* W = static_cast<ST*>(scratch);
   ST* gu = W + items * p.n;
   int32_t* st = reinterpret_cast<int32_t*>(gu + items);
-  const size_t smem = DHB + AW * WSB;
+  const size_t smem = DHB + AW * AdjWs<D>::BYTES;
   auto k1 = k_adjoint_points<D, ST>;
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
