@@ -73,6 +73,25 @@ def instances(seed: int):
     return out
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(value: float, world: int) -> float:
+    """Maximum of `value` over the ranks (the job's time is its slowest rank's).  A CPU tensor
+    for gloo, a device tensor for NCCL; no-op for one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seeds(rank: int, per_rank: int) -> list:
+    """Seeds of the independent instances a rank advances (weak scaling: disjoint per rank)."""
+    return [rank * per_rank + b for b in range(per_rank)]
+
+
 # ------------------------------------------------------------------ oracle leg (CPU)
 def _oracle_points(task):
     """Worker: oracle frozen-velocity update of the given points (one instance)."""
@@ -282,10 +301,7 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
         clk = clocks.stop()
         L.lmep_sync_status(h)
         total_ms = float(sum(step_ms))
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world)
         pts = N_POINTS * len(insts) * args.steps * world
         # roofline of the n = 13 launches
         f32 = f64 = 0.0
@@ -330,10 +346,7 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
         for k in u0:                    # next step's input is this step's output
             host_in[k].copy_(host_out[k])
     e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, world)
     results["e2e"] = {"value": N_POINTS * len(insts) * e2e_steps * world / (e2e_total * 1e-3), "unit": UNIT,
                       "h2d_bytes_per_step": N_POINTS * len(insts) * 4,
                       "d2h_bytes_per_step": N_POINTS * len(insts) * 4}
@@ -447,10 +460,7 @@ def allen_cahn_main(args, rank, world, local_rank, cores):
     clk = clocks.stop()
     ms = a.elapsed_time(b)
     L.lmep_sync_status(prob.handle)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     pts = prob.points * args.steps * world
     # e2e: host state in, one step, host state out (pinned), through the public API
     hin = u.detach().cpu().pin_memory()
@@ -597,8 +607,9 @@ def adjoint_main(args, rank, world, local_rank, cores):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     p = adj_problem(K)
-    u0 = np.stack([wl.burgers_ic(ADJ_N, rank * B + b) for b in range(B)]).astype(np.float32)
-    tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + rank * B + b) for b in range(B)]),
+    seeds = rank_seeds(rank, B)
+    u0 = np.stack([wl.burgers_ic(ADJ_N, q) for q in seeds]).astype(np.float32)
+    tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + q) for q in seeds]),
                        dtype=torch.float32, device=dev)
     solver = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="mixed", checkpoint_every=2)
     x0 = torch.tensor(u0, device=dev)
@@ -627,10 +638,7 @@ def adjoint_main(args, rank, world, local_rank, cores):
     clk = clocks.stop()
     L.lmep_sync_status(solver.handle)
     total = t_fwd + t_bwd
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
+    total = max_over_ranks(total, world)
     pts = ADJ_N * B * K * world
     # roofline of the adjoint kernel: launches timed alone on the initial states
     grid = solver.grid(B)
