@@ -720,6 +720,136 @@ def adjoint_main(args, rank, world, local_rank, cores):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ stand-alone apply sweep (a6)
+def _oracle_apply(task):
+    """Oracle steps of a periodic instance: time per point-update on a bounded size."""
+    N, n, scheme, steps = task
+    import numpy as np
+    import workloads as wl
+    from oracle import lmep as olmep
+    if scheme == "linear":
+        p = wl.Problem("adv", N, -1.0, 1.0, wl.PERIODIC, n, 0.0, c1=-1.0, c2=1e-4, steps=steps)
+        p = p.with_(dt=0.5 * p.h)
+    else:
+        p = wl.allen_cahn(N, n=n, scheme="etdrk2", steps=steps)
+    u0 = np.sin(np.pi * p.nodes()) * 0.5
+    t0 = time.perf_counter()
+    olmep.run(p, u0, steps)
+    return N * steps, time.perf_counter() - t0
+
+
+def apply_sweep_main(args, rank, world, local_rank, cores):
+    """One periodic instance of 2^k points per rank: linear advection-diffusion (one stencil) and
+    Allen-Cahn ETDRK2 (two stencils and N(.) on the fly), n in {5, 9, 15} (linear) and {5, 9, 13}
+    (ETDRK2), FP32 and FP64 state.
+    Bytes per point-update: read u once, write u+ once."""
+    import numpy as np
+    N = 1 << args.sweep_log2n
+    K = max(10, min(args.steps, 200))
+    pool = None
+    if rank == 0 and world == 1 and args.impl == "own":
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(cores, 6))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(cores, 6))
+        t0 = time.perf_counter()
+        pts = 0
+        for k in range(args.steps):
+            res = pool.map(_oracle_apply, [(4096, n, "linear", 1) for n in (5, 9, 15)] +
+                           [(4096, n, "etdrk2", 1) for n in (5, 9, 13)])
+            pts += sum(r[0] for r in res)
+        dt = time.perf_counter() - t0
+        pool.close()
+        v = pts / dt
+        print(json.dumps({"impl": "reference", "metric": "point-updates/s of the stored-weight apply", "value": v,
+                          "unit": "point-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": f"oracle apply, 6 cases of N = 4096 per step"},
+                          "cpu_baseline": {"value": v, "unit": "point-updates/s", "cores": min(cores, 6),
+                                           "kind": "oracle", "sample": "one step of the six cases at N = 4096"},
+                          "e2e": {"value": v, "unit": "point-updates/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}), flush=True)
+        return
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    h = L.Handle()
+    peak, peak_src = measured_hbm_peak()
+    rows = []
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    for prec in ("mixed", "fp64"):
+        es = 4 if prec == "mixed" else 8
+        dt_ = L.state_dtype(prec)
+        x = torch.linspace(-1.0, 1.0, N + 1, dtype=torch.float64, device=dev)[:-1]
+        u = (0.5 * torch.sin(np.pi * x) + 0.05 * torch.sin(40 * np.pi * x)).to(dt_)
+        w = torch.empty_like(u)
+        # ETDRK2 harvests (n + 2)-row augmented matrices, so its widest stencil is n = 13
+        for n, scheme, nonlin in [(n_, "linear", "none") for n_ in (5, 9, 15)] + \
+                                 [(n_, "etdrk2", "allen_cahn") for n_ in (5, 9, 13)]:
+            hh = 2.0 / N
+            if scheme == "linear":
+                op = L.Operator(c1=-1.0, c2=1e-4 * hh)
+                dtv = 0.5 * hh
+                nphi = 0
+            else:
+                op = L.Operator(c2=1e-4)
+                dtv = 0.5 * hh * hh / 1e-4
+                nphi = 2
+            g = L.Grid(N=N, h=hh, bc="periodic", n=n)
+            W = torch.empty(n, 1 + nphi, n, dtype=dt_, device=dev)
+            L.lmep_harvest_weights(h, g, op, dtv, nphi, None, W, prec)
+            L.lmep_step(h, g, op, scheme, nonlin, dtv, W, u, w, 4, prec)       # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            L.lmep_step(h, g, op, scheme, nonlin, dtv, W, u, w, K, prec)
+            b.record()
+            b.synchronize()
+            ms = max_over_ranks(a.elapsed_time(b) / K, world)
+            gbs = 2.0 * es * N / (ms * 1e-3) / 1e9
+            rows.append({"precision": prec, "n": n, "scheme": scheme, "ms_per_step": ms, "GB_s": gbs,
+                         "frac": gbs / peak})
+    clk = clocks.stop()
+    L.lmep_sync_status(h)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    head = next(r for r in rows if r["precision"] == "mixed" and r["n"] == 9 and r["scheme"] == "linear")
+    cpu = None
+    if pool is not None:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_apply, [(16384, nn, "linear", 2) for nn in (5, 9, 15)] +
+                       [(16384, nn, "etdrk2", 2) for nn in (5, 9, 13)])
+        dt = time.perf_counter() - t0
+        pool.close()
+        cpu = {"value": sum(r[0] for r in res) / dt, "unit": "point-updates/s", "cores": min(cores, 6),
+               "kind": "oracle", "sample": f"two steps of the six cases at N = 16384 ({dt:.1f} s)"}
+    line = {"metric": "HBM throughput of the stored-weight banded apply (single instance)",
+            "value": N * world / (head["ms_per_step"] * 1e-3), "unit": "point-updates/s", "n_gpus": world,
+            "steps": K, "warmup": 4, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (headline row); sweep has f32 and f64",
+            "data": "synthetic",
+            "config": {"workload": f"periodic instance of N = 2^{args.sweep_log2n} on [-1,1): linear advection-"
+                                   "diffusion (c = 1, mu = 1e-4 h, dt = h/2) and Allen-Cahn ETDRK2 (eps^2 = 1e-4, "
+                                   "dt = h^2/2/eps^2); headline row FP32 linear n = 9",
+                       "l2": f"state {2 * 4 * N >> 20} MiB (FP32) / {2 * 8 * N >> 20} MiB (FP64), larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": head["GB_s"], "peak": peak, "unit": "GB/s",
+                         "frac": head["frac"], "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_apply_stream<float, linear, n = 9>",
+                         "algorithmic_bytes_per_launch": 8.0 * N},
+            "sweep": rows, "cpu_baseline": cpu,
+            "e2e": None, "gpu_launches": len(rows) * (K + 4), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -730,9 +860,11 @@ def main():
                     help="oracle points per instance for cpu_baseline (0: every interior point of the step)")
     ap.add_argument("--cpu-points", type=float, default=12e6,
                     help="Allen-Cahn cpu_baseline: oracle point-updates (whole instances in batch order)")
-    ap.add_argument("--workload", choices=["burgers", "allen_cahn", "adjoint"], default="burgers",
+    ap.add_argument("--workload", choices=["burgers", "allen_cahn", "adjoint", "apply_sweep"], default="burgers",
                     help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply; "
-                         "adjoint: forward + reverse sweep of the frozen-velocity step (gradient)")
+                         "adjoint: forward + reverse sweep of the frozen-velocity step (gradient); "
+                         "apply_sweep: the stored-weight apply on one large instance (HBM roofline)")
+    ap.add_argument("--sweep-log2n", type=int, default=26, help="apply_sweep: log2 of the instance size")
     ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
     ap.add_argument("--adj-batch", type=int, default=8, help="adjoint workload: Burgers instances per launch")
     ap.add_argument("--adj-steps", type=int, default=4, help="adjoint workload: forward + reverse steps timed")
@@ -747,6 +879,8 @@ def main():
         return allen_cahn_main(args, rank, world, local_rank, cores)
     if args.workload == "adjoint":
         return adjoint_main(args, rank, world, local_rank, cores)
+    if args.workload == "apply_sweep":
+        return apply_sweep_main(args, rank, world, local_rank, cores)
 
     if args.impl == "reference":
         if rank != 0:
