@@ -176,6 +176,11 @@ def step_cases():
         "ac_etdrk2_neumann": (wl.allen_cahn(1531, bc=wl.NEUMANN, n=9, scheme="etdrk2", steps=15), 4),
         "ac_etd1_periodic": (wl.allen_cahn(2049, n=7, scheme="etd1", steps=15), 5),
         "kdv_etdrk2": (wl.kdv(N=3000, n=11, L=30.0, steps=10), None),
+        # widths of the stand-alone apply sweep: n = 5 and 13 for ETDRK2, 15 for the linear apply
+        "ac_etdrk2_n5_periodic": (wl.allen_cahn(3001, n=5, scheme="etdrk2", steps=12), 6),
+        "ac_etdrk2_n13_neumann": (wl.allen_cahn(2500, bc=wl.NEUMANN, n=13, scheme="etdrk2", steps=12), 7),
+        "advdiff_n15_periodic": (wl.Problem("adv", 4099, -1.0, 1.0, wl.PERIODIC, 15, 0.0, c1=-1.0, c2=1e-4,
+                                            steps=12).with_(dt=0.7 * 2.0 / 4099), None),
     }
 
 
