@@ -8,13 +8,16 @@ Workload (one "step"): one time step of frozen-velocity viscous Burgers on
 departure-centred windows.  Every point rebuilds and exponentiates its local
 operator at every step (a1-a6 fused in one launch per instance).
 
-value      point-updates/s of the FP32 form (FP32 Pade products and banded
-           apply, FP64 denominator solve and squaring phase), inputs resident.
+value      point-updates/s of the FP32 form, inputs resident: each row of
+           exp(X) from the finite Taylor series of the nilpotent local matrix
+           (FP32) where its error bound allows, else Pade scaling and squaring
+           (FP32 products, FP64 solve and squarings); FP32 banded apply.
 fp64       the same for the plain FP64 path.
+pade_route the FP32 form with Pade scaling and squaring for every row.
 e2e        the FP32 form through the public API with host buffers: every step
            copies the states in from pinned host memory and the result back.
 roofline   the dominant kernel (the n = 13 launches), ALU-bound: achieved
-           FP64-equivalent FLOP/s of the algorithm's own work per launch.
+           FP32-equivalent FLOP/s of the algorithm's own work per launch.
 cpu_baseline  the FP64 oracle on the host cores (spawn pool) on a bounded
            sample of points of the same step; its outputs also give the
            stated error of both GPU paths.
@@ -51,7 +54,7 @@ P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of the
 # current kernels (profiles/k_warp_frozen_burgers_N65536_n13_cfl4.md and
 # profiles/k_apply_stream_allen_cahn_batch4096_n9.md); set to None when a kernel changes.
-TRAFFIC_K_WARP_13_FLOAT = 0.443904e6 + 0.276480e6
+TRAFFIC_K_WARP_13_FLOAT = None
 TRAFFIC_K_APPLY_STREAM_AC = 253.765632e6 + 196.658688e6
 
 
@@ -159,7 +162,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -198,6 +201,11 @@ class ClockSampler:
 def flops_model(n: int, stats, fp32_form: bool):
     """Algorithmic FLOPs of one point-update given (m, s, a): (FP32 part, FP64 part).
 
+    m = 0 marks a row from the finite series of the nilpotent local matrix in
+    the product type, m = 1 one in FP64 (FP32 form): n - 2 vector-matrix
+    products of 2 d^2 (the first term is a row of X) and n - 1 vector
+    additions; its error bound (a second sequence of the same size, in FP32)
+    is the kernel's own extra work and is not counted.
     Pade products: pi_m matrix products of 2 d^3 (Higham 2005, Table 2.2).
     s = 0 (one harvested row): one row of q_m^-1 p_m = an LU-equivalent solve
     (2/3) d^3 + 2 d^2 plus y^T P (2 d^2; FP32 in the FP32 form).
@@ -208,22 +216,32 @@ def flops_model(n: int, stats, fp32_form: bool):
     import numpy as np
     m, s, a = stats[:, 0], stats[:, 1], stats[:, 2]
     d = float(n)
+    series = m <= 1
+    ser = (n - 2) * 2 * d * d + (n - 1) * d
+    ser64 = m == 1
     prod = np.vectorize(lambda mm: PI_M.get(int(mm), 6))(m) * 2 * d ** 3
     one_row = s == 0
     solve = np.where(one_row, (2.0 / 3.0) * d ** 3 + 2 * d * d, (8.0 / 3.0) * d ** 3)
     ytp = np.where(one_row, 2 * d * d, 0.0)
     sq = a * 2 * d ** 3 + ((2.0 ** (s - a)) - 1) * 2 * d * d
     apply_ = 2 * d
+    lo = np.where(series, np.where(ser64, 0.0, ser), prod + ytp) + apply_   # FP32 in the FP32 form
+    hi = np.where(series, np.where(ser64, ser, 0.0), solve + sq)          # FP64 in both
     if fp32_form:
-        return float(np.sum(prod + apply_ + ytp)), float(np.sum(solve + sq))
-    return 0.0, float(np.sum(prod + apply_ + ytp + solve + sq))
+        return float(np.sum(lo)), float(np.sum(hi))
+    return 0.0, float(np.sum(lo + hi))
 
 
 def gpu_leg(args, rank: int, world: int, local_rank: int):
+    """Each leg advances the nine instances through one captured CUDA graph per step (nine fused
+    frozen-velocity launches, each followed by the API's copy-back of the state), with the L2
+    flushed between steps outside the timed region.  The n = 13 kernels are timed alone from a
+    second graph of two steps per n = 13 instance (ping-pong, no copy-back)."""
     import numpy as np
     import torch
 
     import paper_2603_15964_gb300 as L
+    from paper_2603_15964_gb300.frozen import FrozenInstance, FrozenSet
     import workloads as wl
 
     torch.cuda.set_device(local_rank)
@@ -231,122 +249,108 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
     h = L.Handle()
     seed = rank
     insts = instances(seed)
-    u0 = {}
-    for n, cfl, p in insts:
-        u0[(n, cfl)] = wl.burgers_ic(N_POINTS, seed)
+    keys = [(n, cfl) for n, cfl, _ in insts]
+    u0 = {k: wl.burgers_ic(N_POINTS, seed) for k in keys}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def grid_op(p):
-        return (L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True),
-                L.Operator(c2=p.c2, frozen_adv=1.0))
+    def inst_of(p):
+        return FrozenInstance(L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True),
+                              L.Operator(c2=p.c2, frozen_adv=1.0), p.dt)
+
+    def timed(fn, steps):
+        """Per-step device times (ms) of fn() with the L2 flushed before each step."""
+        out = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
 
     results = {}
-    for prec in ("mixed", "fp64"):
-        dt_ = L.state_dtype(prec)
-        bufs = {}
-        for n, cfl, p in insts:
-            u = torch.tensor(u0[(n, cfl)], dtype=dt_, device=dev)
-            bufs[(n, cfl)] = (u, torch.empty_like(u))
-        # stats (m, s, a) of every point at the initial state, from the kernel itself
+    for key, prec, method in (("mixed", "mixed", "auto"), ("fp64", "fp64", "auto"), ("pade", "mixed", "pade")):
+        fs = FrozenSet([inst_of(p) for _, _, p in insts], precision=prec, method=method, handle=h)
+        fs.load([u0[k] for k in keys])
+        # route statistics (m, s, a) of every point at the initial state, from the kernel itself
         stats = {}
-        for n, cfl, p in insts:
-            g, op = grid_op(p)
+        for k, inst, u in zip(keys, fs.instances, fs.states):
             st = torch.zeros(N_POINTS, 3, dtype=torch.int32, device=dev)
-            L.lmep_frozen_stats(h, g, op, p.dt, bufs[(n, cfl)][0], st, prec)
-            stats[(n, cfl)] = st.cpu().numpy()[1:-1]
+            L.lmep_frozen_stats(h, inst.grid, inst.op, inst.dt, u, st, prec)
+            stats[k] = st.cpu().numpy()[1:-1]
         # first step from u0 (kept for the stated error)
         first = {}
-        for n, cfl, p in insts:
-            g, op = grid_op(p)
-            u, w = bufs[(n, cfl)]
+        for k, inst, u in zip(keys, fs.instances, fs.states):
             v = u.clone()
-            L.lmep_step(h, g, op, "linear", "none", p.dt, None, v, w, 1, prec)
-            first[(n, cfl)] = v.cpu().numpy()
+            L.lmep_step(h, inst.grid, inst.op, "linear", "none", inst.dt, None, v, torch.empty_like(v), 1, prec)
+            first[k] = v.cpu().numpy()
         L.lmep_sync_status(h)
-
-        def one_step(ev=None):
-            for n, cfl, p in insts:
-                g, op = grid_op(p)
-                u, w = bufs[(n, cfl)]
-                if ev is not None and n == 13:
-                    ev[(n, cfl)][0].record(stream)
-                L.lmep_step(h, g, op, "linear", "none", p.dt, None, u, w, 1, prec)
-                if ev is not None and n == 13:
-                    ev[(n, cfl)][1].record(stream)
-
-        for _ in range(args.warmup):
-            one_step()
+        fs.capture()
+        fs.replay(args.warmup)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         clocks = ClockSampler(local_rank)
         clocks.start()
-        step_ms = []
-        kern_ms = {k: [] for k in u0 if k[0] == 13}
         torch.cuda.synchronize()
-        for _ in range(args.steps):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for k in kern_ms}
-            a.record(stream)
-            one_step(ev)
-            b.record(stream)
-            b.synchronize()
-            step_ms.append(a.elapsed_time(b))
-            for k, (e0, e1) in ev.items():
-                kern_ms[k].append(e0.elapsed_time(e1))
+        step_ms = timed(lambda: fs.replay(1), args.steps)
         torch.cuda.synchronize()
         clk = clocks.stop()
         L.lmep_sync_status(h)
-        total_ms = float(sum(step_ms))
-        total_ms = max_over_ranks(total_ms, world)
+        total_ms = max_over_ranks(float(sum(step_ms)), world)
         pts = N_POINTS * len(insts) * args.steps * world
-        # roofline of the n = 13 launches
+        # the n = 13 kernels alone: two steps per instance per replay
+        k13 = [k for k in keys if k[0] == 13]
+        fs13 = FrozenSet([inst_of(p) for n, _, p in insts if n == 13], precision=prec, method=method, handle=h)
+        fs13.load([u0[k] for k in k13])
+        fs13.capture(nsteps=2)
+        fs13.replay(3)
+        reps = max(3, min(args.steps, 200))
+        t13 = 1e-3 * float(sum(timed(lambda: fs13.replay(1), reps)))
+        L.lmep_sync_status(h)
         f32 = f64 = 0.0
-        t13 = 0.0
-        for k, times in kern_ms.items():
+        for k in k13:
             a32, a64 = flops_model(13, stats[k], prec == "mixed")
-            f32 += a32 * len(times)
-            f64 += a64 * len(times)
-            t13 += sum(times) * 1e-3
-        results[prec] = {"value": pts / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
-                         "first": first, "clocks": clk, "f32": f32, "f64": f64, "t13": t13,
-                         "launches13": sum(len(v) for v in kern_ms.values()),
-                         "stats": {f"n{k[0]}_cfl{int(k[1])}": {
-                             "m": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 0], return_counts=True))},
-                             "s": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 1], return_counts=True))}}
-                             for k in stats}}
-    # e2e (FP32 form): host buffers through the public API, copies inside the timed region
-    dt_ = torch.float32
-    host_in = {k: torch.tensor(v, dtype=dt_).pin_memory() for k, v in u0.items()}
-    host_out = {k: torch.empty(N_POINTS, dtype=dt_).pin_memory() for k in u0}
-    dbuf = {k: (torch.empty(N_POINTS, dtype=dt_, device=dev), torch.empty(N_POINTS, dtype=dt_, device=dev))
-            for k in u0}
-    e2e_steps = max(3, min(args.steps, 20))
-    torch.cuda.synchronize()
+            f32 += 2 * reps * a32
+            f64 += 2 * reps * a64
+        results[key] = {"value": pts / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
+                        "first": first, "clocks": clk, "f32": f32, "f64": f64, "t13": t13,
+                        "launches13": 2 * reps * len(k13),
+                        "stats": {f"n{k[0]}_cfl{int(k[1])}": {
+                            "m": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 0], return_counts=True))},
+                            "s": {int(m): int(c) for m, c in zip(*np.unique(stats[k][:, 1], return_counts=True))}}
+                            for k in stats}}
+        del fs, fs13
+    L.lmep_set_expm_method(h, "auto")
+    # e2e (FP32 form) through the public API: every step copies the nine states in from pinned host
+    # memory, replays the step graph and copies the results back (all inside the timed region)
+    fs = FrozenSet([inst_of(p) for _, _, p in insts], precision="mixed", method="auto", handle=h)
+    fs.load([u0[k] for k in keys])
+    fs.capture()
+    host_in = [torch.tensor(u0[k], dtype=torch.float32).pin_memory() for k in keys]
+    host_out = [torch.empty(N_POINTS, dtype=torch.float32).pin_memory() for _ in keys]
+    e2e_steps = max(3, min(args.steps, 200))
+
+    def e2e_step():
+        for u, hi in zip(fs.states, host_in):
+            u.copy_(hi, non_blocking=True)
+        fs.replay(1)
+        for u, ho in zip(fs.states, host_out):
+            ho.copy_(u, non_blocking=True)
+
+    e2e_step()                          # warm-up
+    for hi, ho in zip(host_in, host_out):
+        hi.copy_(ho)
     e2e_ms = []
-    for it in range(e2e_steps + 1):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for n, cfl, p in insts:
-            g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True)
-            op = L.Operator(c2=p.c2, frozen_adv=1.0)
-            u, w = dbuf[(n, cfl)]
-            u.copy_(host_in[(n, cfl)], non_blocking=True)
-            L.lmep_step(h, g, op, "linear", "none", p.dt, None, u, w, 1, "mixed")
-            host_out[(n, cfl)].copy_(u, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if it > 0:                      # the first iteration is a warm-up
-            e2e_ms.append(a.elapsed_time(b))
-        for k in u0:                    # next step's input is this step's output
-            host_in[k].copy_(host_out[k])
-    e2e_total = float(sum(e2e_ms))
-    e2e_total = max_over_ranks(e2e_total, world)
+    for _ in range(e2e_steps):
+        e2e_ms += timed(e2e_step, 1)
+        for hi, ho in zip(host_in, host_out):   # next step's input is this step's output
+            hi.copy_(ho)
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), world)
     results["e2e"] = {"value": N_POINTS * len(insts) * e2e_steps * world / (e2e_total * 1e-3), "unit": UNIT,
                       "h2d_bytes_per_step": N_POINTS * len(insts) * 4,
                       "d2h_bytes_per_step": N_POINTS * len(insts) * 4}
@@ -361,12 +365,12 @@ def stated_error(results, tasks, res):
     import workloads as wl
     out = {}
     scale = max(float(np.max(np.abs(wl.burgers_ic(N_POINTS, 0)))), 1e-300)
-    for prec in ("mixed", "fp64"):
+    for key, name in (("mixed", "fp32_form"), ("fp64", "fp64"), ("pade", "fp32_form_pade_route")):
         worst = 0.0
         for (n, cfl, seed, pts), vals in zip(tasks, res):
-            got = results[prec]["first"][(n, cfl)][pts]
+            got = results[key]["first"][(n, cfl)][pts]
             worst = max(worst, float(np.max(np.abs(got - vals))) / scale)
-        out["fp32_form" if prec == "mixed" else "fp64"] = worst
+        out[name] = worst
     return out
 
 
@@ -853,7 +857,7 @@ def apply_sweep_main(args, rank, world, local_rank, cores):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--cpu-sample", type=int, default=0,
@@ -930,21 +934,32 @@ def main():
     m = res["mixed"]
     t13 = m["t13"]
     p64 = P64_NOMINAL
-    achieved = (m["f64"] + m["f32"] * (p64 / P32_NOMINAL)) / t13
+    p32 = P32_NOMINAL
+    # FP32-equivalent rate: an FP64 FLOP costs P32/P64 FP32 FLOPs, so frac is the time the
+    # launch's FLOPs need at both peaks over the time it took
+    achieved = (m["f32"] + m["f64"] * (p32 / p64)) / t13
     line = {
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64 (FP32 Pade products and banded apply; FP64 solve and squaring)",
+        "vs_baseline": None,
+        "dtype": "f32 (finite-series rows and banded apply in FP32; FP64 window setup; Pade fallback rows: "
+                 "FP32 products, FP64 solve and squaring)",
         "data": "synthetic", "config": workload_config(0),
         "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"], "dtype": "f64"},
+        "pade_route": {"value": res["pade"]["value"], "ms_per_step": res["pade"]["ms_per_step"],
+                       "dtype": "f32+f64 (FP32 Pade products and banded apply; FP64 solve and squaring)",
+                       "avg_launch_ms_n13": 1e3 * res["pade"]["t13"] / res["pade"]["launches13"],
+                       "frac": (res["pade"]["f32"] + res["pade"]["f64"] * (p32 / p64)) / res["pade"]["t13"] / p32},
         "error": {"vs": "FP64 oracle, one step from the initial state, sampled points (cpu_baseline sample)",
                   "rel_linf": err},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p64 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / p64, "traffic": TRAFFIC_K_WARP_13_FLOAT,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / p32, "traffic": TRAFFIC_K_WARP_13_FLOAT,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "kernel": "k_warp<13,float> (frozen-velocity fused step, n = 13)",
-                     "note": "FP64-equivalent rate (F64 + F32 * P64/P32) / t of the algorithm's own FLOPs; "
-                             "peak = GB300 nominal FP64; see measured FMA-chain peaks",
+                     "note": "FP32-equivalent rate (F32 + F64 * P32/P64) / t of the algorithm's own FLOPs "
+                             "(finite-series rows: the series products; Pade rows: products, solve, squarings); "
+                             "peak P32 = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz, P64 = GB300 nominal FP64; "
+                             "see the measured FMA-chain peaks",
                      "f64_tflops": m["f64"] / t13 / 1e12, "f32_tflops": m["f32"] / t13 / 1e12,
                      "measured_fma_peak_fp64_tflops": res["fma_peak_fp64"] / 1e12,
                      "measured_fma_peak_fp32_tflops": res["fma_peak_fp32"] / 1e12,

@@ -17,12 +17,13 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import BC, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
+from ._lib import BC, EXPM, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
 
 __all__ = ["Grid", "Operator", "Handle", "lmep_build_operator", "lmep_expm", "lmep_harvest_weights",
            "lmep_step", "lmep_batch_workspace_bytes", "lmep_batch_prepare", "lmep_step_batched",
            "lmep_step_batched_once",
-           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_sync_status", "lmep_fma_peak",
+           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_set_expm_method", "lmep_sync_status",
+           "lmep_fma_peak",
            "state_dtype", "LmepError"]
 
 
@@ -181,6 +182,12 @@ def lmep_frozen_stats(h: Handle, grid: Grid, op: Operator, dt: float, u, stats, 
                       stream=None) -> None:
     _lib.call("lmep_frozen_stats", h.ptr, C.byref(grid.c()), C.byref(op.c()), dt, _ptr(u), _ptr(stats),
               PREC[precision], _stream(stream))
+
+
+def lmep_set_expm_method(h: Handle, method: str = "auto") -> None:
+    """Frozen-velocity exponential rows of handle h: "auto" (finite series of the nilpotent local
+    matrix, Pade scaling and squaring where its error bound is large) or "pade" (Pade only)."""
+    _lib.call("lmep_set_expm_method", h.ptr, EXPM[method])
 
 
 def lmep_sync_status(h: Handle, stream=None) -> None:

@@ -19,6 +19,7 @@ BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 PREC = {"fp64": 0, "mixed": 1}
 SCHEME = {"linear": 0, "etd1": 1, "etdrk2": 2}
 NONLIN = {"none": 0, "allen_cahn": 1, "kdv": 2}
+EXPM = {"auto": 0, "pade": 1}
 
 
 class LmepGrid(C.Structure):
@@ -66,6 +67,7 @@ _SIGS = {
     "lmep_adjoint_step_noalloc": [C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, _P, _P,
                                   C.c_int32, _P],
     "lmep_frozen_stats": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, C.c_int32, _P],
+    "lmep_set_expm_method": [_P, C.c_int32],
     "lmep_sync_status": [_P, _P],
     "lmep_fma_peak": [C.c_int32, C.POINTER(C.c_double)],
     "lmep_status_string": [C.c_int],

@@ -26,6 +26,7 @@ struct BatchPlan {
 struct lmep_handle {
   int device;
   unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
+  int32_t expm_method = LMEP_EXPM_AUTO;  // frozen-velocity rows (lmep_set_expm_method)
   std::map<const void*, BatchPlan> plans;
 };
 
@@ -203,7 +204,9 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
   if (u_frozen_dev) {
     if (n_phi != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity weights need n_phi == 0");
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen weights need N >= 2n");
-    CK(lmep::launch_frozen(p, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream)), "harvest(frozen)");
+    KParams pf = p;
+    pf.series = h->expm_method == LMEP_EXPM_AUTO;
+    CK(lmep::launch_frozen(pf, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream)), "harvest(frozen)");
     return LMEP_OK;
   }
   if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "frozen operator needs u_frozen_dev");
@@ -236,7 +239,8 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     if (scheme != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity stepping uses the linear scheme");
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen step needs N >= 2n");
     if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "W_dev is NULL but the operator is not frozen");
-    const KParams p = make_params(g, op, dt, 0);
+    KParams p = make_params(g, op, dt, 0);
+    p.series = h->expm_method == LMEP_EXPM_AUTO;
     for (int64_t t = 0; t < nsteps; ++t) {
       CK(lmep::launch_frozen(p, cur, nxt, true, mixed, h->flags, S(stream)), "step(frozen)");
       std::swap(cur, nxt);
@@ -496,9 +500,18 @@ lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_ope
   if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "lmep_frozen_stats needs a frozen operator");
   if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
   if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann needs N >= 2n");
-  CK(lmep::launch_frozen(make_params(g, op, dt, 0), u_dev, nullptr, false, precision == LMEP_PREC_MIXED, h->flags,
-                         S(stream), stats_dev),
+  KParams p = make_params(g, op, dt, 0);
+  p.series = h->expm_method == LMEP_EXPM_AUTO;
+  CK(lmep::launch_frozen(p, u_dev, nullptr, false, precision == LMEP_PREC_MIXED, h->flags, S(stream), stats_dev),
      "frozen_stats");
+  return LMEP_OK;
+}
+
+lmep_status lmep_set_expm_method(lmep_handle* h, int32_t method) {
+  if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
+  if (method != LMEP_EXPM_AUTO && method != LMEP_EXPM_PADE)
+    return fail(LMEP_ERR_INVALID, "method must be LMEP_EXPM_AUTO or LMEP_EXPM_PADE");
+  h->expm_method = method;
   return LMEP_OK;
 }
 

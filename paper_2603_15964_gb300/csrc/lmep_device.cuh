@@ -872,6 +872,140 @@ __device__ void powers_and_scaling(const Ws<PT>& w, const Lay<D, PT>& L, int lan
   __syncwarp();
 }
 
+// ---------------------------------------------------------------- finite series (a4)
+// Without the identity term the local matrix X = c1h Dh1 + c2h Dh2 + c3h Dh3
+// is a polynomial without constant term in the differentiation matrix of the
+// window's interpolating polynomial (degree < n, Sec. 2): X^n = 0, and a row
+// of its exponential is the finite sum
+//   e_r^T exp(X) = sum_{k < n} e_r^T X^k / k!
+// exactly: n - 2 vector-matrix products instead of the Pade products, the
+// solve and the squarings.  In floating point the terms can cancel (a large
+// ||X|| with a row of order one); the computed row then differs from the exact
+// one by about u * beta, beta = sum_k ||e_r^T |X|^k||_1 / k! (u the unit
+// roundoff of PT), which is accumulated in FP32 next to the series and
+// returned.  The caller keeps the row when beta is small and otherwise falls
+// back to Pade scaling and squaring.
+//
+// Several points run side by side in one warp, GS lanes each (a group of
+// aligned lanes; column j = lane % GS of the group's point, j < n holds column
+// j of X in registers).  The row vector is broadcast through the group's
+// ping-pong buffers (VPP PT / WPP floats apart, 16-byte aligned, read back
+// with 16-byte loads), so that one __syncwarp per term orders their reuse.  The FP32 form runs two FMA chains
+// per term (latency); the FP64 path one (the FP64 pipe is the limit).  `row`
+// receives element j of the row (0 for j >= n); the cI term is not included
+// (it factors out as e^cI).  All lanes of the warp must call this together.
+// Sum over the GS aligned lanes of a group; every lane of the group receives
+// the same value (each butterfly stage adds the same two operands on both sides).
+template <int GS, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = GS / 2; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+// |x| of a column entry for the bound: free in FP32 (an operand modifier), an
+// integer-only truncation for doubles (keeps the FP64 pipe free).
+template <typename PT>
+struct AbsCol {
+  float a;
+  __device__ __forceinline__ void set(PT x) {
+    if constexpr (sizeof(PT) == 8) a = approx_abs_f32(x);
+  }
+  __device__ __forceinline__ float get(PT x) const {
+    if constexpr (sizeof(PT) == 8) return a;
+    else return fabsf(x);
+  }
+};
+
+template <int D, typename PT, int GS, int VPP, int WPP>
+__device__ __forceinline__ float group_series_row(const Asm& as, int j, int r, PT* vb, float* wb, PT& row) {
+  constexpr bool F32 = sizeof(PT) == 4;
+  static_assert(D <= GS && GS % 4 == 0, "one lane per column; whole float4 / double2 broadcasts");
+  constexpr int VW = F32 ? 4 : 2;  // PT entries per 16-byte broadcast load
+  PT x[D];
+  AbsCol<PT> ax[D];
+  const bool col = j < as.n;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    PT v = PT(0);
+    if (col && i < as.n) {
+      const int o = i * LD + j;
+      if constexpr (F32) {
+        v = as.c1f * as.Dhf[o];
+        v = fmaf(as.c2f, as.Dhf[DMAX * LD + o], v);
+        v = fmaf(as.c3f, as.Dhf[2 * DMAX * LD + o], v);
+      } else {
+        v = as.c1h * as.Dh[o];
+        v = fma(as.c2h, as.Dh[DMAX * LD + o], v);
+        if (as.c3h != 0.0) v = fma(as.c3h, as.Dh[2 * DMAX * LD + o], v);
+      }
+    }
+    x[i] = v;
+    ax[i].set(v);
+  }
+  // k = 1: row r of X
+  PT v = PT(0);
+  float wv = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    if (i == r) {
+      v = x[i];
+      wv = ax[i].get(x[i]);
+    }
+  PT acc = (j == r ? PT(1) : PT(0)) + v;
+  float sw = wv;
+#pragma unroll
+  for (int k = 2; k < D; ++k) {
+    PT* vk = vb + (k & 1) * VPP;
+    float* wk = wb + (k & 1) * WPP;
+    vk[j] = v;
+    wk[j] = wv;
+    __syncwarp();
+    PT s0 = PT(0), s1 = PT(0);
+    float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+    for (int q = 0; q < (D + VW - 1) / VW; ++q) {
+      PT vv[VW];
+      if constexpr (F32) {
+        const float4 t = reinterpret_cast<const float4*>(vk)[q];
+        vv[0] = t.x; vv[1] = t.y; vv[2] = t.z; vv[3] = t.w;
+      } else {
+        const double2 t = reinterpret_cast<const double2*>(vk)[q];
+        vv[0] = t.x; vv[1] = t.y;
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        const int i = q * VW + e;
+        if (i < D) {
+          if (F32 && (i & 1)) s1 = fma(vv[e], x[i], s1);
+          else s0 = fma(vv[e], x[i], s0);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < (D + 3) / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4*>(wk)[q];
+      const float ww[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = 4 * q + e;
+        if (i < D) {
+          if (i & 1) t1 = fmaf(ww[e], ax[i].get(x[i]), t1);
+          else t0 = fmaf(ww[e], ax[i].get(x[i]), t0);
+        }
+      }
+    }
+    v = (F32 ? s0 + s1 : s0) * PT(1.0 / double(k));
+    wv = (t0 + t1) * float(1.0 / double(k));
+    acc += v;
+    sw += wv;
+  }
+  row = acc;
+  const float beta = 1.0f + group_sum<GS>(sw);
+  __syncwarp();  // the buffers are free for the caller
+  return beta;
+}
+
 // exp(X) for X = w.X64 (D x D, double).  Writes the harvested rows
 // rows[0..nrows) into w.V[q*DMAX + j] (double) when full == false, or the
 // whole exponential into E (stride lde) when full == true.  m_out, s_out and

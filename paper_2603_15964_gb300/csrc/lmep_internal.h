@@ -23,6 +23,9 @@ struct KParams {
   // and their FP32 roundings for the FP32 form
   double dt_h, c0dt, c2h, c3h;
   float c0dt_f, c2h_f, c3h_f;
+  // frozen-velocity rows: 1 = finite series of the nilpotent local matrix with
+  // a Pade scaling-and-squaring fallback, 0 = Pade scaling and squaring only
+  int series;
 };
 
 // Set the thread-local text returned by lmep_last_error().

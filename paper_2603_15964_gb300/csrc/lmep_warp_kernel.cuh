@@ -17,6 +17,8 @@
 // (a6), so the weights never reach HBM.
 #pragma once
 
+#include <atomic>
+
 #include "lmep_device.cuh"
 #include "lmep_internal.h"
 
@@ -43,6 +45,7 @@ struct WarpJob {
   unsigned* flags;
   const double* dh;     // h^k D^(k) tables of this n (device, FP64 and FP32), not MODE_FULL
   const float* dhf;
+  int64_t span;         // frozen modes: consecutive points per warp (set by run_warp)
 };
 
 // X = cI I + c1h Dh1 + c2h Dh2 + c3h Dh3 on the n x n window, zero-padded to D.
@@ -79,6 +82,202 @@ __device__ __forceinline__ void augment(double* X64, int n, int n_phi, int r, do
 template <typename PT>
 constexpr int ctas_per_sm() { return sizeof(PT) == 4 ? 4 : 3; }
 
+// Largest error bound beta at which a frozen-velocity row is taken from the
+// finite series; above it the row comes from Pade scaling and squaring.  The
+// computed series stays within about 2 u beta of the exact row (u the unit
+// roundoff of the summation type) on the Burgers distributions (nu = 1e-6 to
+// 1e-3, n = 5..13, CFL 1..4), so these keep it below 2e-6 (FP32 sums in the
+// FP32 form), 2.5e-10 (FP64 sums in the FP32 form) and 1.5e-14 (FP64 path),
+// inside the parity tolerances of 1e-5 (FP32 form) and 1e-12 (FP64 path).
+constexpr float SERIES_TAU_F32 = 16.0f;
+constexpr float SERIES_TAU_F32_FORM_F64 = 1048576.0f;  // 2^20
+constexpr float SERIES_TAU_F64 = 64.0f;
+
+// Frozen-velocity points side by side in the finite series: GS lanes per point.
+template <int D>
+struct Groups {
+  static constexpr int GS = D <= 4 ? 4 : (D <= 8 ? 8 : 16);
+  static constexpr int G = 32 / GS;
+};
+// PT entries between the groups' broadcast buffers (two more for doubles, which
+// moves the groups' 16-byte loads to different banks) and per ping-pong half.
+template <int D, typename PT>
+struct SeriesBuf {
+  static constexpr int VS = Groups<D>::GS + (sizeof(PT) == 8 ? 2 : 0);
+  static constexpr int VPP = Groups<D>::G * VS;
+  static constexpr int WPP = 32;
+  static constexpr int BYTES = 2 * VPP * int(sizeof(PT)) + 2 * WPP * 4;
+};
+
+// Finite-series rows (product type QT) of the chunk's points in `todo` (bit q
+// = point c + q), G at a time: group g = lane / GS takes the g-th remaining
+// point.  A row whose error bound is at most tau is stored (MODE_FROZEN_W) or
+// applied to its window and handed to its point's lane in `res` (and, with
+// statistics, its degree entry set to mcode); the points whose bound is larger
+// are returned.  The per-point values hr, c1h, c1f, st and base live in the
+// point's own lane.
+template <int D, typename QT, typename ST>
+__device__ __forceinline__ unsigned series_points(const WarpJob& job, const double* Dh, const float* Dhf,
+                                                  unsigned todo, int lane, int hr, double c1h, float c1f,
+                                                  int64_t st, int64_t base, QT* vb, float* wb, float tau, QT e0,
+                                                  int64_t c, int mcode, ST& res) {
+  constexpr int GS = Groups<D>::GS, G = Groups<D>::G;
+  using SB = SeriesBuf<D, QT>;
+  const KParams& p = job.p;
+  const int n = p.n;
+  const int mode = job.mode;
+  const ST* u = static_cast<const ST*>(job.u);
+  ST* out = static_cast<ST*>(job.out);
+  const int g = lane / GS, j = lane % GS;
+  QT* vg = vb + g * SB::VS;
+  float* wg = wb + g * GS;
+  bool failed = false;
+  while (todo) {
+    unsigned t = todo;
+    for (int k = 0; k < g; ++k) t &= t - 1;
+    const int q = t ? __ffs(t) - 1 : -1;
+#pragma unroll
+    for (int k = 0; k < G; ++k) todo &= todo - 1;
+    const bool has = q >= 0;
+    const int qs = has ? q : 0;
+    const int hr_q = __shfl_sync(FULL, hr, qs);
+    const int64_t st_q = __shfl_sync(FULL, st, qs);
+    const int64_t base_q = __shfl_sync(FULL, base, qs);
+    Asm as{Dh, Dhf, n, 0.0, 0.0, p.c2h, p.c3h, 0.0f, 0.0f, p.c2h_f, p.c3h_f};
+    if constexpr (sizeof(QT) == 4) as.c1f = __shfl_sync(FULL, c1f, qs);
+    else as.c1h = __shfl_sync(FULL, c1h, qs);
+    // the window values are loaded first so that their latency hides behind the series
+    ST uw = ST(0);
+    if (mode == MODE_FROZEN_STEP && has && j < n) uw = u[base_q + grid_index(st_q + j, p.N, p.bc)];
+    QT row;
+    const float beta = group_series_row<D, QT, GS, SB::VPP, SB::WPP>(as, j, hr_q, vg, wg, row);
+    row *= e0;
+    const bool ok = has && beta <= tau;
+    if (mode == MODE_FROZEN_W && out && ok && j < n) out[(c + q) * n + j] = ST(row);
+    const QT acc = group_sum<GS>(row * QT(uw));
+    // each group's result to its point's lane
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+      const int qk = __shfl_sync(FULL, q, k * GS);
+      const QT ak = __shfl_sync(FULL, acc, k * GS);
+      const bool okk = __shfl_sync(FULL, ok, k * GS);
+      if (lane == qk) {
+        if (okk) {
+          res = ST(ak);
+          if (job.ms && mcode) job.ms[3 * (c + qk)] = mcode;
+        } else {
+          failed = true;
+        }
+      }
+    }
+  }
+  return __ballot_sync(FULL, failed);
+}
+
+// One chunk of the frozen-velocity modes: the points c .. min(c + 32, end) - 1.
+// Lane l first prepares point c + l -- its value (one coalesced load for the
+// chunk), departure shift, window, re-centring -- so that the scalar FP64 work
+// of 32 points takes one pass.  The rows then come from, in order:
+//   1. the finite series in the product type, G points side by side;
+//   2. (FP32 form) the finite series in FP64 for the points 1 rejected --
+//      at nu = 1e-6 the few next to Dirichlet walls, where the one-sided
+//      second-derivative rows have large weights;
+//   3. Pade scaling and squaring on the whole warp, one point at a time, for
+//      the rest (every point when p.series == 0).
+// Each result returns to its point's lane and the chunk leaves in one
+// coalesced store.
+template <int D, typename PT>
+__device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w, const double* Dh,
+                                             const float* Dhf, int64_t c, int64_t end, int lane, unsigned& bad) {
+  using ST = PT;
+  constexpr bool F32 = sizeof(PT) == 4;
+  const KParams& p = job.p;
+  const int n = p.n;
+  const int mode = job.mode;
+  const ST* u = static_cast<const ST*>(job.u);
+  ST* out = static_cast<ST*>(job.out);
+  // ---- lane-parallel preparation of point c + lane
+  const int64_t it = c + lane;
+  const bool valid = it < end;
+  int64_t b = 0, i = 0;
+  if (valid) split_index(it, p.N, p.batch, b, i);
+  const bool wall = valid && p.bc == BC_DIRICHLET && (i == 0 || i == p.N - 1);
+  const bool live = valid && !wall;  // walls keep their values and get no weights
+  const int64_t base = b * p.N;
+  const double ui = live ? double(u[base + i]) : 0.0;
+  const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
+  const int64_t st = window_start(i, p.N, n, p.bc, k);
+  const int r = int(i - st);
+  const double a1 = p.c1 - p.fa * ui;
+  const int kr = recentring_shift(a1, p.dt_h, n, r);
+  const double c1h = fma(a1, p.dt_h, double(kr));
+  const float c1f = F32 ? __double2float_rn(c1h) : 0.0f;
+  const int hr = r - kr;
+  ST res = ST(0);
+  if (job.ms && live) {  // series rows (m = 0); FP64-series and Pade rows overwrite m below
+    job.ms[3 * it] = 0;
+    job.ms[3 * it + 1] = 0;
+    job.ms[3 * it + 2] = 0;
+  }
+  unsigned pade = __ballot_sync(FULL, live);
+  if (p.series) {
+    // e^{dt c0}: the identity term, left out of the nilpotent part
+    const double e0 = p.c0dt != 0.0 ? exp(p.c0dt) : 1.0;
+    PT* vb = w.M(4);  // broadcast buffers in the Pade workspace, which the series does not use
+    float* wb = reinterpret_cast<float*>(vb + 2 * SeriesBuf<D, PT>::VPP);
+    pade = series_points<D, PT, ST>(job, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vb, wb,
+                                    F32 ? SERIES_TAU_F32 : SERIES_TAU_F64, PT(e0), c, 0, res);
+    if constexpr (F32) {
+      if (pade) {
+        double* vd = reinterpret_cast<double*>(w.M(4));
+        float* wd = reinterpret_cast<float*>(vd + 2 * SeriesBuf<D, double>::VPP);
+        pade = series_points<D, double, ST>(job, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vd, wd,
+                                            SERIES_TAU_F32_FORM_F64, e0, c, 1, res);
+      }
+    }
+  }
+  // ---- Pade scaling and squaring, one point at a time on the whole warp
+  while (pade) {
+    const int q = __ffs(pade) - 1;
+    pade &= pade - 1;
+    const int hr_q = __shfl_sync(FULL, hr, q);
+    const int64_t st_q = __shfl_sync(FULL, st, q);
+    const int64_t base_q = __shfl_sync(FULL, base, q);
+    const double c1h_q = __shfl_sync(FULL, c1h, q);
+    Asm as{Dh, Dhf, n, p.c0dt, c1h_q, p.c2h, p.c3h, p.c0dt_f, 0.0f, p.c2h_f, p.c3h_f};
+    if constexpr (F32) as.c1f = __shfl_sync(FULL, c1f, q);  // X is assembled in FP32
+    ST uw = ST(0);
+    if (mode == MODE_FROZEN_STEP && lane < n) uw = u[base_q + grid_index(st_q + lane, p.N, p.bc)];
+    if constexpr (!F32) {
+      assemble<D>(w.X64, Dh, n, p.c0dt, c1h_q, p.c2h, p.c3h, lane);
+      __syncwarp();
+    }
+    int mq, sq, aq;
+    warp_expm<D, PT>(w, lane, &hr_q, 1, false, nullptr, 0, &mq, &sq, &aq, F32 ? &as : nullptr);
+    const PT row = lane < n ? PT(w.V[lane]) : PT(0);
+    if (mode == MODE_FROZEN_W && out && lane < n) out[(c + q) * n + lane] = ST(row);
+    const ST acc = warp_sum(ST(row) * uw);
+    if (lane == q) {
+      res = acc;
+      if (job.ms) {
+        job.ms[3 * it] = mq;
+        job.ms[3 * it + 1] = sq;
+        job.ms[3 * it + 2] = aq;
+      }
+    }
+    __syncwarp();
+  }
+  // ---- the chunk's results
+  if (out && wall) {
+    if (mode == MODE_FROZEN_STEP) out[it] = ST(i == 0 ? p.bc_lo : p.bc_hi);
+    else for (int jj = 0; jj < n; ++jj) out[it * n + jj] = ST(0);
+  }
+  if (out && live && mode == MODE_FROZEN_STEP) {
+    out[it] = res;
+    bad |= !isfinite(res);
+  }
+}
+
 template <int D, typename PT>
 __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob job) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -98,10 +297,22 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
   }
   __syncthreads();
   using ST = PT;
-  const ST* u = static_cast<const ST*>(job.u);
   ST* out = static_cast<ST*>(job.out);
-  const bool dir = p.bc == BC_DIRICHLET;
   unsigned bad = 0;
+  if (mode >= MODE_FROZEN_W) {
+    static_assert(SeriesBuf<D, PT>::BYTES <= DMAX * Ws<PT>::LDM * int(sizeof(PT)) &&
+                      SeriesBuf<D, double>::BYTES <= DMAX * Ws<PT>::LDM * int(sizeof(PT)),
+                  "the series buffers fit in one product matrix");
+    // one contiguous range of points per warp (every warp of the grid is resident),
+    // in chunks of equal size up to 32
+    const int64_t begin = (int64_t(blockIdx.x) * WARPS + warp) * job.span;
+    const int64_t end = begin + job.span < job.items ? begin + job.span : job.items;
+    const int64_t csz = (job.span + (job.span + 31) / 32 - 1) / ((job.span + 31) / 32);
+    for (int64_t c = begin; c < end; c += csz)
+      frozen_chunk<D, PT>(job, w, Dh, Dhf, c, c + csz < end ? c + csz : end, lane, bad);
+    if (bad) atomicOr(job.flags, 1u);
+    return;
+  }
   for (int64_t it = int64_t(blockIdx.x) * WARPS + warp; it < job.items; it += int64_t(gridDim.x) * WARPS) {
     if (mode == MODE_FULL) {
       for (int e = lane; e < D * D; e += 32) w.X64[(e / D) * LD + e % D] = job.A[it * D * D + e];
@@ -144,78 +355,54 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       __syncwarp();
       continue;
     }
-    // frozen velocity: point i of instance b (instances of N points back to back)
-    int64_t b, i;
-    split_index(it, p.N, p.batch, b, i);
-    const ST* ub = u + b * p.N;
-    if (dir && (i == 0 || i == p.N - 1)) {  // walls keep their values; no weights
-      if (out) {
-        if (mode == MODE_FROZEN_STEP) {
-          if (lane == 0) out[it] = ST(i == 0 ? p.bc_lo : p.bc_hi);
-        } else {
-          for (int j = lane; j < n; j += 32) out[it * n + j] = ST(0);
-        }
-      }
-      continue;
-    }
-    const double ui = double(ub[i]);
-    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
-    const int64_t st = window_start(i, p.N, n, p.bc, k);
-    const int r = int(i - st);
-    const double a1 = p.c1 - p.fa * ui;
-    const int kr = recentring_shift(a1, p.dt_h, n, r);
-    const double c1h = fma(a1, p.dt_h, double(kr));
-    Asm as{Dh, Dhf, n, p.c0dt, c1h, p.c2h, p.c3h, p.c0dt_f, 0.0f, p.c2h_f, p.c3h_f};
-    if (sizeof(PT) == 4) {
-      as.c1f = __double2float_rn(c1h);  // X is assembled in FP32 inside warp_expm
-    } else {
-      assemble<D>(w.X64, Dh, n, p.c0dt, c1h, p.c2h, p.c3h, lane);
-      __syncwarp();
-    }
-    const int hr = r - kr;
-    // the window values are loaded now so that their latency hides behind the expm
-    ST uw = ST(0);
-    if (mode == MODE_FROZEN_STEP && lane < n) uw = ub[grid_index(st + lane, p.N, p.bc)];
-    int m_, s_, a_;
-    warp_expm<D, PT>(w, lane, &hr, 1, false, nullptr, 0, &m_, &s_, &a_, sizeof(PT) == 4 ? &as : nullptr);
-    if (job.ms && lane == 0) {
-      job.ms[3 * it] = m_;
-      job.ms[3 * it + 1] = s_;
-      job.ms[3 * it + 2] = a_;
-    }
-    if (!out) {
-      __syncwarp();
-      continue;
-    }
-    if (mode == MODE_FROZEN_STEP) {
-      ST acc = ST(0);
-      if (lane < n) acc = ST(w.V[lane]) * uw;
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        out[it] = acc;
-        bad |= !isfinite(acc);
-      }
-    } else {
-      if (lane < n) out[it * n + lane] = ST(w.V[lane]);
-    }
-    __syncwarp();
   }
   if (bad) atomicOr(job.flags, 1u);
 }
 
+// Resident CTAs per SM of k_warp<D, PT>, set up once per device (the shared
+// memory attribute and the occupancy query are host calls worth skipping on
+// every launch); 0 on failure, with the error in *err.
 template <int D, typename PT>
-cudaError_t run_warp(const WarpJob& job, cudaStream_t s) {
-  const size_t smem = dh_bytes<PT>() + WARPS * Ws<PT>::BYTES;
+int warp_ctas_per_sm(size_t smem, cudaError_t* err) {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess || dev < 0 || dev >= 64) {
+    if (*err == cudaSuccess) *err = cudaErrorInvalidDevice;
+    return 0;
+  }
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
   auto k = k_warp<D, PT>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
+  *err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (*err != cudaSuccess) return 0;
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * WARPS, smem);
-  if (per_sm < 1) per_sm = 1;
+  *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * WARPS, smem);
+  if (*err != cudaSuccess) return 0;
+  v = per_sm < 1 ? 1 : per_sm;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+template <int D, typename PT>
+cudaError_t run_warp(const WarpJob& job_in, cudaStream_t s) {
+  const size_t smem = dh_bytes<PT>() + WARPS * Ws<PT>::BYTES;
+  cudaError_t e = cudaSuccess;
+  const int per_sm = warp_ctas_per_sm<D, PT>(smem, &e);
+  if (per_sm == 0) return e;
   const int64_t cap = int64_t(device_info().sms) * per_sm;
-  const int64_t need = (job.items + WARPS - 1) / WARPS;
+  WarpJob job = job_in;
+  int64_t need;
+  need = (job.items + WARPS - 1) / WARPS;
+  if (job.mode >= MODE_FROZEN_W) {
+    // frozen modes: every warp of the grid (all resident) takes one contiguous
+    // range of points, so that the SMs finish together
+    const int64_t g = need < cap ? (need > 0 ? need : 1) : cap;
+    job.span = (job.items + g * WARPS - 1) / (g * WARPS);
+    if (job.span < 1) job.span = 1;
+  }
   const int grid = int(need < cap ? (need > 0 ? need : 1) : cap);
-  k<<<grid, 32 * WARPS, smem, s>>>(job);
+  k_warp<D, PT><<<grid, 32 * WARPS, smem, s>>>(job);
   return cudaGetLastError();
 }
 

@@ -126,17 +126,25 @@ def test_harvest_constant(L, H, precision, name):
 
 
 # ------------------------------------------------------------------ (a1)-(a5) frozen velocity
+@pytest.mark.parametrize("method", ["auto", "pade"])
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("n,cfl", [(7, 1.0), (9, 2.0), (13, 4.0), (13, 1.0), (5, 3.0)])
-@pytest.mark.parametrize("nu", [1e-6, 1e-3])
-def test_harvest_frozen(L, H, precision, n, cfl, nu):
+@pytest.mark.parametrize("nu", [1e-6, 4e-4, 1e-3])
+def test_harvest_frozen(L, H, precision, n, cfl, nu, method):
+    """Both evaluations of the exponential row ("auto": finite series of the nilpotent local
+    matrix where its error bound is small, Pade elsewhere; "pade": Pade only).  At N = 513 the
+    viscosities 4e-4 and 1e-3 give launches where both routes run side by side."""
     N = 513
     p = wl.burgers(N=N, n=n, cfl=cfl, nu=nu)
     u = wl.burgers_ic(N, 0)
     if precision == "mixed":
         u = u.astype(np.float32).astype(np.float64)     # both sides see the same FP32 state
     W = torch.empty(N, n, dtype=L.state_dtype(precision), device="cuda")
-    L.lmep_harvest_weights(H, grid_of(p), op_of(p), p.dt, 0, dev(u, L.state_dtype(precision)), W, precision)
+    L.lmep_set_expm_method(H, method)
+    try:
+        L.lmep_harvest_weights(H, grid_of(p), op_of(p), p.dt, 0, dev(u, L.state_dtype(precision)), W, precision)
+    finally:
+        L.lmep_set_expm_method(H, "auto")
     got = W.cpu().numpy()
     D = oop.unit_D(n)
     want = np.zeros((N, n))
@@ -150,8 +158,6 @@ def test_harvest_frozen(L, H, precision, n, cfl, nu):
     # scaling and squaring -- the oracle's included -- is only good to ~1e-11
     # there.  Where the two differ by more than 1e-12 the exact rows decide: the
     # GPU must be at least as accurate as the oracle (within 2x).
-    mp = pytest.importorskip("mpmath")
-    from test_oracle_adjoint_exact import exact_row
     diff = np.max(np.abs(got - want), axis=1) / np.maximum(np.sum(np.abs(want), axis=1), 1e-300)
     diff[0] = diff[-1] = 0.0
     worst = [int(i) for i in np.argsort(-diff)[:12] if diff[i] > 1e-12]
@@ -164,6 +170,24 @@ def test_harvest_frozen(L, H, precision, n, cfl, nu):
         e_orc.append(np.max(np.abs(want[i] - ex)) / den)
     if worst:
         assert max(e_gpu) <= max(2 * max(e_orc), 1e-12), (worst, e_gpu, e_orc)
+
+
+def exact_row(n, a_hat, mu_hat, r):
+    """Row r of exp(a_hat D-hat1 + mu_hat D-hat2) in exact rational arithmetic: the local matrix
+    is nilpotent, so the Taylor series ends after n terms (a double is a rational number)."""
+    from fractions import Fraction
+    from oracle import exact
+    D1 = exact.lagrange_D(range(n), 1)
+    D2 = exact.lagrange_D(range(n), 2)
+    a, mu = Fraction(a_hat), Fraction(mu_hat)
+    X = [[a * D1[i][j] + mu * D2[i][j] for j in range(n)] for i in range(n)]
+    v = [Fraction(int(j == r)) for j in range(n)]
+    acc = v[:]
+    for k in range(1, n + 1):
+        v = [sum(v[i] * X[i][j] for i in range(n)) / k for j in range(n)]
+        acc = [acc[j] + v[j] for j in range(n)]
+    assert all(x == 0 for x in v)            # X^n = 0 exactly
+    return np.array([float(x) for x in acc])
 
 
 # ------------------------------------------------------------------ (a6) stored weights
