@@ -9,9 +9,11 @@ departure-centred windows.  Every point rebuilds and exponentiates its local
 operator at every step (a1-a6 fused in one launch per instance).
 
 value      point-updates/s of the FP32 form, inputs resident: each row of
-           exp(X) from the finite Taylor series of the nilpotent local matrix
-           (FP32) where its error bound allows, else Pade scaling and squaring
-           (FP32 products, FP64 solve and squarings); FP32 banded apply.
+           exp(X), X = a D1 + E, as l(r + a)^T exp(E) (Lagrange weights times
+           the exponential of the point-independent part, computed once per
+           instance in FP64) where its bound allows, else from the finite
+           Taylor series of the nilpotent local matrix, else Pade scaling and
+           squaring; FP32 apply.
 fp64       the same for the plain FP64 path.
 pade_route the FP32 form with Pade scaling and squaring for every row.
 e2e        the FP32 form through the public API with host buffers: every step
@@ -201,6 +203,9 @@ class ClockSampler:
 def flops_model(n: int, stats, fp32_form: bool):
     """Algorithmic FLOPs of one point-update given (m, s, a): (FP32 part, FP64 part).
 
+    m = 2 marks a factorised row l(r + a)^T exp(E) (FP32 form): the Lagrange
+    weights by prefix and suffix products (4 d), one vector-matrix product
+    with exp(E) (2 d^2) and the bound sum_j |l_j| R_j (2 d).
     m = 0 marks a row from the finite series of the nilpotent local matrix in
     the product type, m = 1 one in FP64 (FP32 form): n - 2 vector-matrix
     products of 2 d^2 (the first term is a row of X) and n - 1 vector
@@ -225,8 +230,11 @@ def flops_model(n: int, stats, fp32_form: bool):
     ytp = np.where(one_row, 2 * d * d, 0.0)
     sq = a * 2 * d ** 3 + ((2.0 ** (s - a)) - 1) * 2 * d * d
     apply_ = 2 * d
+    fact = m == 2
     lo = np.where(series, np.where(ser64, 0.0, ser), prod + ytp) + apply_   # FP32 in the FP32 form
     hi = np.where(series, np.where(ser64, ser, 0.0), solve + sq)          # FP64 in both
+    lo = np.where(fact, 2 * d * d + 6 * d + apply_, lo)
+    hi = np.where(fact, 0.0, hi)
     if fp32_form:
         return float(np.sum(lo)), float(np.sum(hi))
     return 0.0, float(np.sum(lo + hi))
@@ -942,8 +950,8 @@ def main():
         "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (finite-series rows and banded apply in FP32; FP64 window setup; Pade fallback rows: "
-                 "FP32 products, FP64 solve and squaring)",
+        "dtype": "f32 (factorised rows l^T exp(E) and apply in FP32, exp(E) once per instance in FP64; "
+                 "FP64 window setup; fallback rows: finite series, Pade)",
         "data": "synthetic", "config": workload_config(0),
         "fp64": {"value": res["fp64"]["value"], "ms_per_step": res["fp64"]["ms_per_step"], "dtype": "f64"},
         "pade_route": {"value": res["pade"]["value"], "ms_per_step": res["pade"]["ms_per_step"],

@@ -60,7 +60,7 @@ typedef enum { LMEP_BC_PERIODIC = 0, LMEP_BC_DIRICHLET = 1, LMEP_BC_NEUMANN = 2 
 typedef enum { LMEP_PREC_FP64 = 0, LMEP_PREC_MIXED = 1 } lmep_precision;
 typedef enum { LMEP_SCHEME_LINEAR = 0, LMEP_SCHEME_ETD1 = 1, LMEP_SCHEME_ETDRK2 = 2 } lmep_scheme;
 typedef enum { LMEP_N_NONE = 0, LMEP_N_ALLEN_CAHN = 1, LMEP_N_KDV = 2 } lmep_nonlin;
-typedef enum { LMEP_EXPM_AUTO = 0, LMEP_EXPM_PADE = 1 } lmep_expm_method;
+typedef enum { LMEP_EXPM_AUTO = 0, LMEP_EXPM_PADE = 1, LMEP_EXPM_SERIES = 2 } lmep_expm_method;
 
 /* Uniform 1-D grid and stencil (Sec. 2.1 step 1).
  *  N      number of points.  Periodic: x_j = x0 + j h, j < N.  Dirichlet and
@@ -239,7 +239,8 @@ LMEP_API lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_op
  * exactly as the fused step chooses them for state u_dev (the remaining
  * 2^(s-a) - 1 squaring factors act on the harvested row only); (0, 0, 0)
  * marks a row taken from the finite series in the precision's product type,
- * (1, 0, 0) one taken from the finite series in FP64 (FP32 form only; see
+ * (1, 0, 0) one taken from the finite series in FP64 (FP32 form only) and
+ * (2, 0, 0) one taken from the factorised form (FP32 form only; see
  * lmep_set_expm_method).  Runs the
  * frozen-velocity kernel without writing weights.  Dirichlet wall points are
  * left untouched.  u_dev: state dtype of `precision`; stats_dev: int32[N][3]. */
@@ -249,18 +250,28 @@ LMEP_API lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const
 /* How the frozen-velocity launches of handle h (lmep_step and
  * lmep_harvest_weights with a frozen operator, lmep_frozen_stats) evaluate a
  * row of exp(X) (Sec. 2.1 step 4).  Without its identity term the local
- * matrix is a polynomial without constant term in the window's
- * differentiation matrix, hence nilpotent (X^n = 0 on n nodes), and a row of
- * its exponential is the finite Taylor sum of n terms.
- *  LMEP_EXPM_AUTO (the default): that finite sum, with an a-posteriori error
- *         bound per point, beta = sum_k |row of |X|^k|_1 / k! (the computed
- *         row is within about 2 u beta of the exact one, u the unit
- *         roundoff).  The FP32 form sums in FP32 while beta <= 16, else in
- *         FP64 while beta <= 2^20; the FP64 path in FP64 while beta <= 64; a
- *         point with a larger bound takes the PADE route.
+ * matrix X = a Dh1 + E, E = c2h Dh2 + c3h Dh3, is a polynomial without
+ * constant term in the window's differentiation matrix: it is nilpotent
+ * (X^n = 0 on n nodes), so a row of its exponential is the finite Taylor sum
+ * of n terms, and its parts commute, so row r of exp(X) is l(r + a)^T exp(E)
+ * with l the Lagrange weights of the window (Thm. 1) and exp(E) the same for
+ * every point.
+ *  LMEP_EXPM_SERIES: the finite sum, with an a-posteriori error bound per
+ *         point, beta = sum_k |row of |X|^k|_1 / k! (the computed row is
+ *         within about 2 u beta of the exact one, u the unit roundoff).  The
+ *         FP32 form sums in FP32 while beta <= 16, else in FP64 while
+ *         beta <= 2^20; the FP64 path in FP64 while beta <= 64; a point with
+ *         a larger bound takes the PADE route.
+ *  LMEP_EXPM_AUTO (the default): in the FP32 form, first the factorised row
+ *         l(r + a)^T exp(E), where its bound sum_j |l_j| |row j of exp(E)|_1
+ *         is at most 16, the rest as SERIES; exp(E) is computed once per
+ *         (n, dt c2 / h^2, dt c3 / h^3) in FP64 (Pade) and kept in the handle
+ *         (the first call for an operator synchronises `stream` once; inside a
+ *         stream capture an operator not seen before takes SERIES).  The FP64
+ *         path as SERIES.
  *  LMEP_EXPM_PADE: Pade scaling and squaring (Higham 2005; Al-Mohy and
  *         Higham 2009) for every point.
- * Both routes meet the same parity tolerances.  Other calls are unaffected.
+ * All routes meet the same parity tolerances.  Other calls are unaffected.
  * Returns LMEP_ERR_INVALID for a NULL handle or an unknown method. */
 LMEP_API lmep_status lmep_set_expm_method(lmep_handle* h, int32_t method);
 

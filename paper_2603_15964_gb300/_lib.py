@@ -19,7 +19,7 @@ BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 PREC = {"fp64": 0, "mixed": 1}
 SCHEME = {"linear": 0, "etd1": 1, "etdrk2": 2}
 NONLIN = {"none": 0, "allen_cahn": 1, "kdv": 2}
-EXPM = {"auto": 0, "pade": 1}
+EXPM = {"auto": 0, "pade": 1, "series": 2}
 
 
 class LmepGrid(C.Structure):

@@ -1,10 +1,13 @@
 // lmep_api.cu -- the C ABI of include/lmep.h: argument checks, dispatch,
 // status flags and the batch workspace.  All compute runs in the kernels of
 // lmep_expm.cu, lmep_apply.cu and lmep_adjoint.cu.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lmep.h"
@@ -27,6 +30,11 @@ struct lmep_handle {
   int device;
   unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
   int32_t expm_method = LMEP_EXPM_AUTO;  // frozen-velocity rows (lmep_set_expm_method)
+  // FP32-form factorised rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP32, n x n then
+  // the n absolute row sums), computed once on the device (sl_scratch) and kept on the host
+  double* sl_scratch = nullptr;
+  std::mutex sl_mu;
+  std::map<std::tuple<int, uint64_t, uint64_t>, std::vector<float>> sl_cache;
   std::map<const void*, BatchPlan> plans;
 };
 
@@ -98,6 +106,53 @@ KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+uint64_t bits_of(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof b);
+  return b;
+}
+
+// exp(E), E = c2h Dh2 + c3h Dh3, of a frozen operator for the FP32 form's factorised rows
+// (n x n FP32, then the n absolute row sums), from the handle's cache or computed now:
+// one FP64 Pade launch on `stream` and a synchronisation, so only outside a stream
+// capture.  *table = nullptr when it is not available (capture, cache full, non-finite);
+// the rows then take the finite series.
+lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, const float** table) {
+  *table = nullptr;
+  const auto key = std::make_tuple(p.n, bits_of(p.c2h), bits_of(p.c3h));
+  std::lock_guard<std::mutex> lock(h->sl_mu);
+  auto it = h->sl_cache.find(key);
+  if (it != h->sl_cache.end()) {
+    *table = it->second.empty() ? nullptr : it->second.data();
+    return LMEP_OK;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(stream, &cs), "cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone || h->sl_cache.size() >= 4096) return LMEP_OK;
+  if (!h->sl_scratch) CK(cudaMalloc(&h->sl_scratch, sizeof(double) * 16 * 16), "cudaMalloc(exp table)");
+  CK(lmep::launch_exp_const(p, h->sl_scratch, stream), "exp(E)");
+  const int n = p.n;
+  std::vector<double> e(size_t(n) * n);
+  CK(cudaMemcpyAsync(e.data(), h->sl_scratch, sizeof(double) * n * n, cudaMemcpyDeviceToHost, stream), "read exp(E)");
+  CK(cudaStreamSynchronize(stream), "exp(E)");
+  std::vector<float> t(size_t(n) * n + n);
+  bool finite = true;
+  for (int j = 0; j < n; ++j) {
+    double rs = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double v = e[size_t(j) * n + k];
+      finite = finite && std::isfinite(v);
+      t[size_t(j) * n + k] = float(v);
+      rs += std::fabs(v);
+    }
+    t[size_t(n) * n + j] = float(rs);
+  }
+  if (!finite) t.clear();  // remembered: this operator takes the finite series
+  auto ins = h->sl_cache.emplace(key, std::move(t)).first;
+  *table = ins->second.empty() ? nullptr : ins->second.data();
+  return LMEP_OK;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int default_tile(bool mixed) { return mixed ? 2048 : 1024; }
@@ -156,6 +211,7 @@ lmep_status lmep_create(lmep_handle** out) {
 lmep_status lmep_destroy(lmep_handle* h) {
   if (!h) return LMEP_OK;
   cudaFree(h->flags);
+  if (h->sl_scratch) cudaFree(h->sl_scratch);
   delete h;
   return LMEP_OK;
 }
@@ -205,8 +261,11 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
     if (n_phi != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity weights need n_phi == 0");
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen weights need N >= 2n");
     KParams pf = p;
-    pf.series = h->expm_method == LMEP_EXPM_AUTO;
-    CK(lmep::launch_frozen(pf, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream)), "harvest(frozen)");
+    pf.series = h->expm_method != LMEP_EXPM_PADE;
+    const float* sl = nullptr;
+    if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, pf, S(stream), &sl)) != LMEP_OK) return st;
+    CK(lmep::launch_frozen(pf, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream), nullptr, sl),
+       "harvest(frozen)");
     return LMEP_OK;
   }
   if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "frozen operator needs u_frozen_dev");
@@ -240,9 +299,11 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen step needs N >= 2n");
     if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "W_dev is NULL but the operator is not frozen");
     KParams p = make_params(g, op, dt, 0);
-    p.series = h->expm_method == LMEP_EXPM_AUTO;
+    p.series = h->expm_method != LMEP_EXPM_PADE;
+    const float* sl = nullptr;
+    if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
     for (int64_t t = 0; t < nsteps; ++t) {
-      CK(lmep::launch_frozen(p, cur, nxt, true, mixed, h->flags, S(stream)), "step(frozen)");
+      CK(lmep::launch_frozen(p, cur, nxt, true, mixed, h->flags, S(stream), nullptr, sl), "step(frozen)");
       std::swap(cur, nxt);
     }
   } else {
@@ -501,16 +562,18 @@ lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_ope
   if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
   if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann needs N >= 2n");
   KParams p = make_params(g, op, dt, 0);
-  p.series = h->expm_method == LMEP_EXPM_AUTO;
-  CK(lmep::launch_frozen(p, u_dev, nullptr, false, precision == LMEP_PREC_MIXED, h->flags, S(stream), stats_dev),
-     "frozen_stats");
+  p.series = h->expm_method != LMEP_EXPM_PADE;
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  const float* sl = nullptr;
+  if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
+  CK(lmep::launch_frozen(p, u_dev, nullptr, false, mixed, h->flags, S(stream), stats_dev, sl), "frozen_stats");
   return LMEP_OK;
 }
 
 lmep_status lmep_set_expm_method(lmep_handle* h, int32_t method) {
   if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
-  if (method != LMEP_EXPM_AUTO && method != LMEP_EXPM_PADE)
-    return fail(LMEP_ERR_INVALID, "method must be LMEP_EXPM_AUTO or LMEP_EXPM_PADE");
+  if (method != LMEP_EXPM_AUTO && method != LMEP_EXPM_PADE && method != LMEP_EXPM_SERIES)
+    return fail(LMEP_ERR_INVALID, "method must be LMEP_EXPM_AUTO, LMEP_EXPM_PADE or LMEP_EXPM_SERIES");
   h->expm_method = method;
   return LMEP_OK;
 }

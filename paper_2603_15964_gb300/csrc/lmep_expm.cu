@@ -202,12 +202,53 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
   return mixed ? warp_job_f32(p.n + p.n_phi, job, s) : warp_job_f64(p.n + p.n_phi, job, s);
 }
 
+// exp(E) of the point-independent part E = c2h Dh2 + c3h Dh3 of a
+// frozen-velocity local matrix: one warp, FP64 Pade scaling and squaring,
+// row-major D x D into out.
+template <int D>
+__global__ void __launch_bounds__(32) k_exp_const(KParams p, const double* dh, double* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* Dh = reinterpret_cast<double*>(smem);
+  Ws<double> w(smem + DH_BYTES);
+  const int lane = threadIdx.x;
+  for (int e = lane; e < 3 * DMAX * LD; e += 32) Dh[e] = dh[e];
+  __syncwarp();
+  assemble<D>(w.X64, Dh, p.n, 0.0, 0.0, p.c2h, p.c3h, lane);
+  __syncwarp();
+  int m, s;
+  warp_expm<D, double>(w, lane, nullptr, 0, true, out, D, &m, &s);
+}
+
+cudaError_t launch_exp_const(const KParams& p, double* out, cudaStream_t s) {
+  const double* d;
+  const float* f;
+  cudaError_t e = fornberg_of(p.n, &d, &f);
+  if (e != cudaSuccess) return e;
+  const size_t smem = DH_BYTES + Ws<double>::BYTES;
+  switch (p.n) {
+    case 3: k_exp_const<3><<<1, 32, smem, s>>>(p, d, out); break;
+    case 5: k_exp_const<5><<<1, 32, smem, s>>>(p, d, out); break;
+    case 7: k_exp_const<7><<<1, 32, smem, s>>>(p, d, out); break;
+    case 9: k_exp_const<9><<<1, 32, smem, s>>>(p, d, out); break;
+    case 11: k_exp_const<11><<<1, 32, smem, s>>>(p, d, out); break;
+    case 13: k_exp_const<13><<<1, 32, smem, s>>>(p, d, out); break;
+    case 15: k_exp_const<15><<<1, 32, smem, s>>>(p, d, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
-                          unsigned* flags, cudaStream_t s, int32_t* stats) {
+                          unsigned* flags, cudaStream_t s, int32_t* stats, const float* sl) {
   if (p.n_phi != 0) return cudaErrorInvalidValue;
   WarpJob job{};
   job.mode = fused ? MODE_FROZEN_STEP : MODE_FROZEN_W;
   job.p = p;
+  if (sl && mixed) {
+    job.sl = 1;
+    for (int e = 0; e < p.n * p.n; ++e) job.slm[e] = sl[e];
+    for (int j = 0; j < p.n; ++j) job.slr[j] = sl[p.n * p.n + j];
+  }
   cudaError_t e = fornberg_of(p.n, &job.dh, &job.dhf);
   if (e != cudaSuccess) return e;
   job.items = p.N * (p.batch > 1 ? p.batch : 1);

@@ -46,7 +46,45 @@ struct WarpJob {
   const double* dh;     // h^k D^(k) tables of this n (device, FP64 and FP32), not MODE_FULL
   const float* dhf;
   int64_t span;         // frozen modes: consecutive points per warp (set by run_warp)
+  // FP32 form, frozen modes: exp(E) of the point-independent part E = c2h Dh2 +
+  // c3h Dh3 of the local matrix (row-major, D x D) and its absolute row sums;
+  // sl == 0 when unavailable.  Read as kernel parameters (constant operands).
+  int sl;
+  float slm[DMAX * DMAX];
+  float slr[DMAX];
 };
+
+// Largest error bound sum_j |l_j| R_j (R_j the absolute row sums of exp(E)) at
+// which a frozen-velocity row of the FP32 form is taken from the factorised
+// form l(z)^T exp(E); the computed row is within a few u32 times the bound of
+// the exact one.
+constexpr float SL_TAU = 16.0f;
+
+// 1 / prod_{m != j} (j - m): the denominators of the Lagrange basis on the
+// integer nodes 0..n-1.
+__host__ __device__ constexpr double lagrange_den(int n, int j) {
+  double d = 1.0;
+  for (int m = 0; m < n; ++m)
+    if (m != j) d *= double(j - m);
+  return 1.0 / d;
+}
+
+// Row z of the advection exponential on the window: the Lagrange weights l_j(z)
+// of the nodes 0..n-1 (Thm. 1: row r of exp(a Dh1) is l(r + a)), by prefix
+// and suffix products (no division by z - j, exact at the nodes).
+template <int D>
+__device__ __forceinline__ void lagrange_weights(float z, float (&l)[D]) {
+  float suf[D];
+  suf[D - 1] = 1.0f;
+#pragma unroll
+  for (int j = D - 1; j > 0; --j) suf[j - 1] = suf[j] * (z - float(j));
+  float pre = 1.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    l[j] = pre * suf[j] * float(lagrange_den(D, j));
+    pre *= z - float(j);
+  }
+}
 
 // X = cI I + c1h Dh1 + c2h Dh2 + c3h Dh3 on the n x n window, zero-padded to D.
 template <int D>
@@ -214,12 +252,43 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
   const float c1f = F32 ? __double2float_rn(c1h) : 0.0f;
   const int hr = r - kr;
   ST res = ST(0);
-  if (job.ms && live) {  // series rows (m = 0); FP64-series and Pade rows overwrite m below
+  if (job.ms && live) {  // series rows (m = 0); the other routes overwrite m below
     job.ms[3 * it] = 0;
     job.ms[3 * it + 1] = 0;
     job.ms[3 * it + 2] = 0;
   }
-  unsigned pade = __ballot_sync(FULL, live);
+  bool done = false;
+  if constexpr (F32) {
+    // 0. (FP32 form) the factorised row: X = a Dh1 + E with E = c2h Dh2 + c3h Dh3
+    //    the same for every point, and the derivative matrices of the window
+    //    commute (they are powers of one differentiation matrix on the local
+    //    polynomial space), so e_r^T exp(X) = e_r^T exp(a Dh1) exp(E) = l(r + a)^T
+    //    exp(E) (Thm. 1 and Thm. 2); exp(E) comes with the launch
+    if (job.sl && live) {
+      float l[D];
+      lagrange_weights<D>(float(hr) + c1f, l);  // r + a = (r - kr) + (a + kr)
+      float bound = 0.0f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) bound = fmaf(fabsf(l[j]), job.slr[j], bound);
+      if (bound <= SL_TAU) {
+        const float e0f = p.c0dt != 0.0 ? float(exp(p.c0dt)) : 1.0f;
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float rk = 0.0f;
+#pragma unroll
+          for (int j = 0; j < D; ++j) rk = fmaf(l[j], job.slm[j * D + k], rk);
+          rk *= e0f;
+          if (mode == MODE_FROZEN_STEP) acc = fmaf(rk, float(u[base + grid_index(st + k, p.N, p.bc)]), acc);
+          else if (out) out[it * n + k] = ST(rk);
+        }
+        res = ST(acc);
+        done = true;
+        if (job.ms) job.ms[3 * it] = 2;
+      }
+    }
+  }
+  unsigned pade = __ballot_sync(FULL, live && !done);
   if (p.series) {
     // e^{dt c0}: the identity term, left out of the nilpotent part
     const double e0 = p.c0dt != 0.0 ? exp(p.c0dt) : 1.0;

@@ -126,14 +126,15 @@ def test_harvest_constant(L, H, precision, name):
 
 
 # ------------------------------------------------------------------ (a1)-(a5) frozen velocity
-@pytest.mark.parametrize("method", ["auto", "pade"])
+@pytest.mark.parametrize("method", ["auto", "series", "pade"])
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("n,cfl", [(7, 1.0), (9, 2.0), (13, 4.0), (13, 1.0), (5, 3.0)])
 @pytest.mark.parametrize("nu", [1e-6, 4e-4, 1e-3])
 def test_harvest_frozen(L, H, precision, n, cfl, nu, method):
-    """Both evaluations of the exponential row ("auto": finite series of the nilpotent local
-    matrix where its error bound is small, Pade elsewhere; "pade": Pade only).  At N = 513 the
-    viscosities 4e-4 and 1e-3 give launches where both routes run side by side."""
+    """Every evaluation of the exponential row ("series": finite series of the nilpotent local
+    matrix where its error bound is small, Pade elsewhere; "auto": in the FP32 form the factorised
+    row l(r + a)^T exp(E) first, then as "series"; "pade": Pade only).  At N = 513 the viscosities
+    4e-4 and 1e-3 give launches where several routes run side by side."""
     N = 513
     p = wl.burgers(N=N, n=n, cfl=cfl, nu=nu)
     u = wl.burgers_ic(N, 0)
