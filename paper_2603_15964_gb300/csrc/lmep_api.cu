@@ -101,6 +101,9 @@ KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int 
   p.c0dt_f = float(p.c0dt);
   p.c2h_f = float(p.c2h);
   p.c3h_f = float(p.c3h);
+  p.c1_f = float(p.c1);
+  p.fa_f = float(p.fa);
+  p.dt_h_f = float(p.dt_h);
   return p;
 }
 

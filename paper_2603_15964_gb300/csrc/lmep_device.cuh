@@ -171,6 +171,19 @@ __device__ __forceinline__ int departure_shift(double u, double dt, double h, in
   const double k = fmax(double(-hs), fmin(double(hs), floor(t)));
   return int(k);
 }
+// departure_shift of a float state for the FP32 form: the estimate in FP32 (error
+// below 4e-7 (|t| + 1) for t = u dt / h + 1/2), the exact FP64 decision when it
+// lies within 1e-6 (|t| + 1) of an integer (or is not finite).
+template <typename P>
+__device__ __forceinline__ int departure_shift_f32(float u, const P& p, int n) {
+  const int hs = (n - 1) >> 1;
+  const float t = fmaf(u, p.dt_h_f, 0.5f);
+  const float f = t - floorf(t);
+  const float m = 1e-6f * (fabsf(t) + 1.0f);
+  if (!(f > m && f < 1.0f - m)) return departure_shift(double(u), p.dt, p.h, n, p.dt_h);
+  return int(fmaxf(float(-hs), fminf(float(hs), floorf(t))));
+}
+
 // Exact integer re-centring of an exponential row: row r of exp(X(a)) equals
 // row r - k of exp(X(a) + k Dh1) (both evaluate e^{dt L} p at the same
 // departure point, Thm. 2).  k is the rounded local Courant number

@@ -23,6 +23,7 @@ struct KParams {
   // and their FP32 roundings for the FP32 form
   double dt_h, c0dt, c2h, c3h;
   float c0dt_f, c2h_f, c3h_f;
+  float c1_f, fa_f, dt_h_f;  // FP32 roundings of c1, fa and dt/h (FP32-form window setup)
   // frozen-velocity rows: 1 = finite series of the nilpotent local matrix with
   // a Pade scaling-and-squaring fallback (after the factorised rows, when the
   // launch carries exp(E)), 0 = Pade scaling and squaring only

@@ -242,15 +242,31 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
   const bool wall = valid && p.bc == BC_DIRICHLET && (i == 0 || i == p.N - 1);
   const bool live = valid && !wall;  // walls keep their values and get no weights
   const int64_t base = b * p.N;
-  const double ui = live ? double(u[base + i]) : 0.0;
-  const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
-  const int64_t st = window_start(i, p.N, n, p.bc, k);
-  const int r = int(i - st);
-  const double a1 = p.c1 - p.fa * ui;
-  const int kr = recentring_shift(a1, p.dt_h, n, r);
-  const double c1h = fma(a1, p.dt_h, double(kr));
-  const float c1f = F32 ? __double2float_rn(c1h) : 0.0f;
-  const int hr = r - kr;
+  int64_t st;
+  int hr;
+  double c1h = 0.0;  // FP32 form: formed from c1f below, only for the rows that fall back
+  float c1f = 0.0f;
+  if constexpr (F32) {
+    // in FP32 but for the window's integer decision next to a tie (exact FP64 test)
+    const float uf = live ? float(u[base + i]) : 0.0f;
+    const int k = p.dep ? departure_shift_f32(uf, p, n) : 0;
+    st = window_start(i, p.N, n, p.bc, k);
+    const int r = int(i - st);
+    const float a1 = p.c1_f - p.fa_f * uf;
+    // any re-centring shift in range gives the same row; the rounded one the smallest norm
+    const int kr = int(fmaxf(float(r - (n - 1)), fminf(float(r), floorf(fmaf(-a1, p.dt_h_f, 0.5f)))));
+    c1f = fmaf(a1, p.dt_h_f, float(kr));
+    hr = r - kr;
+  } else {
+    const double ui = live ? double(u[base + i]) : 0.0;
+    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
+    st = window_start(i, p.N, n, p.bc, k);
+    const int r = int(i - st);
+    const double a1 = p.c1 - p.fa * ui;
+    const int kr = recentring_shift(a1, p.dt_h, n, r);
+    c1h = fma(a1, p.dt_h, double(kr));
+    hr = r - kr;
+  }
   ST res = ST(0);
   if (job.ms && live) {  // series rows (m = 0); the other routes overwrite m below
     job.ms[3 * it] = 0;
@@ -298,6 +314,7 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
                                     F32 ? SERIES_TAU_F32 : SERIES_TAU_F64, PT(e0), c, 0, res);
     if constexpr (F32) {
       if (pade) {
+        c1h = double(c1f);
         double* vd = reinterpret_cast<double*>(w.M(4));
         float* wd = reinterpret_cast<float*>(vd + 2 * SeriesBuf<D, double>::VPP);
         pade = series_points<D, double, ST>(job, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vd, wd,
@@ -306,6 +323,7 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
     }
   }
   // ---- Pade scaling and squaring, one point at a time on the whole warp
+  if (F32 && pade) c1h = double(c1f);
   while (pade) {
     const int q = __ffs(pade) - 1;
     pade &= pade - 1;
@@ -357,7 +375,11 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
   const KParams& p = job.p;
   const int mode = job.mode;
   const int n = p.n;
-  if (mode != MODE_FULL) {
+  if (job.sl) {
+    // factorised launches: the few rows that fall back read the tables from global memory
+    Dh = const_cast<double*>(job.dh);
+    if (Dhf) Dhf = const_cast<float*>(job.dhf);
+  } else if (mode != MODE_FULL) {
     // copy the window's derivative tables (built once per device)
     for (int e = threadIdx.x; e < 3 * DMAX * LD; e += blockDim.x) {
       Dh[e] = job.dh[e];
