@@ -56,7 +56,7 @@ P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of the
 # current kernels (profiles/k_warp_frozen_burgers_N65536_n13_cfl4.md and
 # profiles/k_apply_stream_allen_cahn_batch4096_n9.md); set to None when a kernel changes.
-TRAFFIC_K_WARP_13_FLOAT = None
+TRAFFIC_K_WARP_13_FLOAT = 338.176e3 + 1.792e3
 TRAFFIC_K_APPLY_STREAM_AC = 253.765632e6 + 196.658688e6
 
 
@@ -965,7 +965,9 @@ def main():
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "kernel": "k_warp<13,float> (frozen-velocity fused step, n = 13)",
                      "note": "FP32-equivalent rate (F32 + F64 * P32/P64) / t of the algorithm's own FLOPs "
-                             "(finite-series rows: the series products; Pade rows: products, solve, squarings); "
+                             "(factorised rows: Lagrange weights, one product with exp(E), bound, apply; "
+                             "finite-series rows: the series products; Pade rows: products, solve, squarings); "
+                             "the factorised launch is latency-bound, not FLOP-bound; "
                              "peak P32 = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz, P64 = GB300 nominal FP64; "
                              "see the measured FMA-chain peaks",
                      "f64_tflops": m["f64"] / t13 / 1e12, "f32_tflops": m["f32"] / t13 / 1e12,
