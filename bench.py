@@ -980,7 +980,9 @@ def main():
         "e2e": res["e2e"],
         "gpu_launches": len(NS) * len(CFLS) * args.steps,
         "clocks": m["clocks"],
-        "pade_ms_histogram": m["stats"],
+        "route_histogram": {"legend": "m per point (lmep_frozen_stats): 2 factorised row, 0 finite series in "
+                                      "the product type, 1 finite series in FP64, 3..13 Pade degree; s squarings",
+                            "fp32_form": m["stats"]},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
