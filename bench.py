@@ -368,6 +368,36 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
     return results
 
 
+def exact_error(results, n: int = 13, cfl: float = 4.0, count: int = 40):
+    """Error of each leg's first step against exact rational rows (the local matrix is nilpotent:
+    its exponential row is a finite sum, evaluated in Fractions from the exact Lagrange
+    derivative matrices) at `count` seeded points of one instance, relative to max |u0|."""
+    from fractions import Fraction
+    import numpy as np
+    import workloads as wl
+    from oracle import exact, grid as ogrid
+    p = wl.burgers(N=N_POINTS, n=n, cfl=cfl, nu=NU, seed=0)
+    u0 = wl.burgers_ic(N_POINTS, 0)
+    D1, D2 = exact.lagrange_D(range(n), 1), exact.lagrange_D(range(n), 2)
+    rng = np.random.default_rng(99)
+    pts = sorted(set(rng.integers(1, N_POINTS - 1, count - 4).tolist()) | {1, 2, N_POINTS - 3, N_POINTS - 2})
+    scale = float(np.max(np.abs(u0)))
+    worst = {}
+    for i in pts:
+        idx, r = ogrid.stencil(p, i, ogrid.departure_shift(u0[i], p.dt, p.h, n))
+        a, mu = Fraction(-p.dt * u0[i] / p.h), Fraction(p.dt * p.c2 / p.h ** 2)
+        v = [Fraction(int(j == r)) for j in range(n)]
+        row = v[:]
+        for k in range(1, n):
+            v = [sum(v[m] * (a * D1[m][j] + mu * D2[m][j]) for m in range(n)) / k for j in range(n)]
+            row = [row[j] + v[j] for j in range(n)]
+        want = float(sum(row[j] * Fraction(float(u0[q])) for j, q in enumerate(idx)))
+        for key, name in (("mixed", "fp32_form"), ("fp64", "fp64"), ("pade", "fp32_form_pade_route")):
+            got = float(results[key]["first"][(n, cfl)][i])
+            worst[name] = max(worst.get(name, 0.0), abs(got - want) / scale)
+    return worst
+
+
 def stated_error(results, tasks, res):
     import numpy as np
     import workloads as wl
@@ -930,7 +960,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    err = None
+    err = err_exact = None
     if pool is not None:
         tasks, vals, npts, dt = run_oracle_sample(pool, cores, 0, args.cpu_sample)
         pool.close()
@@ -939,6 +969,7 @@ def main():
         cpu = {"value": npts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{what}, one step ({npts} point-updates, {dt:.1f} s)"}
         err = stated_error(res, tasks, vals)
+        err_exact = exact_error(res)
     m = res["mixed"]
     t13 = m["t13"]
     p64 = P64_NOMINAL
@@ -959,7 +990,10 @@ def main():
                        "avg_launch_ms_n13": 1e3 * res["pade"]["t13"] / res["pade"]["launches13"],
                        "frac": (res["pade"]["f32"] + res["pade"]["f64"] * (p32 / p64)) / res["pade"]["t13"] / p32},
         "error": {"vs": "FP64 oracle, one step from the initial state, sampled points (cpu_baseline sample)",
-                  "rel_linf": err},
+                  "rel_linf": err,
+                  "vs_exact": {"what": "exact rational rows (finite series of the nilpotent local matrix in "
+                                       "Fractions) at 40 points of the n = 13, CFL 4 instance, first step",
+                               "rel_linf": err_exact}},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / p32, "traffic": TRAFFIC_K_WARP_13_FLOAT,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",

@@ -186,8 +186,8 @@ def lmep_frozen_stats(h: Handle, grid: Grid, op: Operator, dt: float, u, stats, 
 
 def lmep_set_expm_method(h: Handle, method: str = "auto") -> None:
     """Frozen-velocity exponential rows of handle h: "series" (finite series of the nilpotent local
-    matrix, Pade scaling and squaring where its error bound is large), "auto" (FP32 form: the
-    factorised row l(r + a)^T exp(E) first, then as "series"; FP64 as "series") or "pade"."""
+    matrix, Pade scaling and squaring where its error bound is large), "auto" (the factorised row
+    l(r + a)^T exp(E) first, then as "series") or "pade"."""
     _lib.call("lmep_set_expm_method", h.ptr, EXPM[method])
 
 

@@ -30,11 +30,11 @@ struct lmep_handle {
   int device;
   unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
   int32_t expm_method = LMEP_EXPM_AUTO;  // frozen-velocity rows (lmep_set_expm_method)
-  // FP32-form factorised rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP32, n x n then
-  // the n absolute row sums), computed once on the device (sl_scratch) and kept on the host
+  // factorised frozen-velocity rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP64, n x n
+  // then the n absolute row sums), computed once on the device (sl_scratch) and kept on the host
   double* sl_scratch = nullptr;
   std::mutex sl_mu;
-  std::map<std::tuple<int, uint64_t, uint64_t>, std::vector<float>> sl_cache;
+  std::map<std::tuple<int, uint64_t, uint64_t>, std::vector<double>> sl_cache;
   std::map<const void*, BatchPlan> plans;
 };
 
@@ -115,12 +115,12 @@ uint64_t bits_of(double x) {
   return b;
 }
 
-// exp(E), E = c2h Dh2 + c3h Dh3, of a frozen operator for the FP32 form's factorised rows
-// (n x n FP32, then the n absolute row sums), from the handle's cache or computed now:
+// exp(E), E = c2h Dh2 + c3h Dh3, of a frozen operator for the factorised rows (n x n FP64,
+// then the n absolute row sums), from the handle's cache or computed now:
 // one FP64 Pade launch on `stream` and a synchronisation, so only outside a stream
 // capture.  *table = nullptr when it is not available (capture, cache full, non-finite);
 // the rows then take the finite series.
-lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, const float** table) {
+lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, const double** table) {
   *table = nullptr;
   const auto key = std::make_tuple(p.n, bits_of(p.c2h), bits_of(p.c3h));
   std::lock_guard<std::mutex> lock(h->sl_mu);
@@ -138,17 +138,17 @@ lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, cons
   std::vector<double> e(size_t(n) * n);
   CK(cudaMemcpyAsync(e.data(), h->sl_scratch, sizeof(double) * n * n, cudaMemcpyDeviceToHost, stream), "read exp(E)");
   CK(cudaStreamSynchronize(stream), "exp(E)");
-  std::vector<float> t(size_t(n) * n + n);
+  std::vector<double> t(size_t(n) * n + n);
   bool finite = true;
   for (int j = 0; j < n; ++j) {
     double rs = 0.0;
     for (int k = 0; k < n; ++k) {
       const double v = e[size_t(j) * n + k];
       finite = finite && std::isfinite(v);
-      t[size_t(j) * n + k] = float(v);
+      t[size_t(j) * n + k] = v;
       rs += std::fabs(v);
     }
-    t[size_t(n) * n + j] = float(rs);
+    t[size_t(n) * n + j] = rs;
   }
   if (!finite) t.clear();  // remembered: this operator takes the finite series
   auto ins = h->sl_cache.emplace(key, std::move(t)).first;
@@ -265,8 +265,8 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen weights need N >= 2n");
     KParams pf = p;
     pf.series = h->expm_method != LMEP_EXPM_PADE;
-    const float* sl = nullptr;
-    if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, pf, S(stream), &sl)) != LMEP_OK) return st;
+    const double* sl = nullptr;
+    if (h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, pf, S(stream), &sl)) != LMEP_OK) return st;
     CK(lmep::launch_frozen(pf, u_frozen_dev, W_dev, false, mixed, h->flags, S(stream), nullptr, sl),
        "harvest(frozen)");
     return LMEP_OK;
@@ -303,8 +303,8 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "W_dev is NULL but the operator is not frozen");
     KParams p = make_params(g, op, dt, 0);
     p.series = h->expm_method != LMEP_EXPM_PADE;
-    const float* sl = nullptr;
-    if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
+    const double* sl = nullptr;
+    if (h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
     for (int64_t t = 0; t < nsteps; ++t) {
       CK(lmep::launch_frozen(p, cur, nxt, true, mixed, h->flags, S(stream), nullptr, sl), "step(frozen)");
       std::swap(cur, nxt);
@@ -567,8 +567,8 @@ lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_ope
   KParams p = make_params(g, op, dt, 0);
   p.series = h->expm_method != LMEP_EXPM_PADE;
   const bool mixed = precision == LMEP_PREC_MIXED;
-  const float* sl = nullptr;
-  if (mixed && h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
+  const double* sl = nullptr;
+  if (h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
   CK(lmep::launch_frozen(p, u_dev, nullptr, false, mixed, h->flags, S(stream), stats_dev, sl), "frozen_stats");
   return LMEP_OK;
 }

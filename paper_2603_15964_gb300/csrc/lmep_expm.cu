@@ -239,15 +239,17 @@ cudaError_t launch_exp_const(const KParams& p, double* out, cudaStream_t s) {
 }
 
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
-                          unsigned* flags, cudaStream_t s, int32_t* stats, const float* sl) {
+                          unsigned* flags, cudaStream_t s, int32_t* stats, const double* sl) {
   if (p.n_phi != 0) return cudaErrorInvalidValue;
   WarpJob job{};
   job.mode = fused ? MODE_FROZEN_STEP : MODE_FROZEN_W;
   job.p = p;
-  if (sl && mixed) {
+  if (sl) {
     job.sl = 1;
-    for (int e = 0; e < p.n * p.n; ++e) job.slm[e] = sl[e];
-    for (int j = 0; j < p.n; ++j) job.slr[j] = sl[p.n * p.n + j];
+    for (int e = 0; e < p.n * p.n + p.n; ++e) {
+      if (mixed) job.slt.f[e] = float(sl[e]);
+      else job.slt.d[e] = sl[e];
+    }
   }
   cudaError_t e = fornberg_of(p.n, &job.dh, &job.dhf);
   if (e != cudaSuccess) return e;

@@ -50,10 +50,11 @@ cudaError_t launch_expm(const double* A, int64_t P, int d, double* E, bool mixed
 cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t B, void* W,
                                  bool mixed, cudaStream_t s);
 // Frozen velocity: fused == false writes W[N][n]; fused == true writes u_out.
-// sl (host, FP32 form only, nullable): exp(E) of the point-independent part of the
-// local matrix, n x n row-major, then its n absolute row sums (factorised rows).
+// sl (host, nullable): exp(E) of the point-independent part of the local matrix,
+// n x n row-major, then its n absolute row sums (factorised rows; rounded to FP32
+// for the FP32 form).
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
-                          unsigned* flags, cudaStream_t s, int32_t* stats = nullptr, const float* sl = nullptr);
+                          unsigned* flags, cudaStream_t s, int32_t* stats = nullptr, const double* sl = nullptr);
 // exp(c2h Dh2 + c3h Dh3) of the window (FP64, n x n row-major) into out (device).
 cudaError_t launch_exp_const(const KParams& p, double* out, cudaStream_t s);
 

@@ -46,18 +46,28 @@ struct WarpJob {
   const double* dh;     // h^k D^(k) tables of this n (device, FP64 and FP32), not MODE_FULL
   const float* dhf;
   int64_t span;         // frozen modes: consecutive points per warp (set by run_warp)
-  // FP32 form, frozen modes: exp(E) of the point-independent part E = c2h Dh2 +
-  // c3h Dh3 of the local matrix (row-major, D x D) and its absolute row sums;
-  // sl == 0 when unavailable.  Read as kernel parameters (constant operands).
+  // Frozen modes: exp(E) of the point-independent part E = c2h Dh2 + c3h Dh3 of
+  // the local matrix (row-major, D x D, then its D absolute row sums) in the
+  // product type; sl == 0 when unavailable.  Read as kernel parameters
+  // (constant operands).
   int sl;
-  float slm[DMAX * DMAX];
-  float slr[DMAX];
+  union {
+    float f[DMAX * DMAX + DMAX];
+    double d[DMAX * DMAX + DMAX];
+  } slt;
 };
 
+// Entry e of the exp(E) table of a launch in the product type PT.
+template <typename PT>
+__device__ __forceinline__ PT sl_entry(const WarpJob& job, int e) {
+  if constexpr (sizeof(PT) == 4) return job.slt.f[e];
+  else return job.slt.d[e];
+}
+
 // Largest error bound sum_j |l_j| R_j (R_j the absolute row sums of exp(E)) at
-// which a frozen-velocity row of the FP32 form is taken from the factorised
-// form l(z)^T exp(E); the computed row is within a few u32 times the bound of
-// the exact one.
+// which a frozen-velocity row is taken from the factorised form l(z)^T exp(E);
+// the computed row is within a few units of roundoff times the bound of the
+// exact one.
 constexpr float SL_TAU = 16.0f;
 
 // 1 / prod_{m != j} (j - m): the denominators of the Lagrange basis on the
@@ -72,17 +82,17 @@ __host__ __device__ constexpr double lagrange_den(int n, int j) {
 // Row z of the advection exponential on the window: the Lagrange weights l_j(z)
 // of the nodes 0..n-1 (Thm. 1: row r of exp(a Dh1) is l(r + a)), by prefix
 // and suffix products (no division by z - j, exact at the nodes).
-template <int D>
-__device__ __forceinline__ void lagrange_weights(float z, float (&l)[D]) {
-  float suf[D];
-  suf[D - 1] = 1.0f;
+template <int D, typename T>
+__device__ __forceinline__ void lagrange_weights(T z, T (&l)[D]) {
+  T suf[D];
+  suf[D - 1] = T(1);
 #pragma unroll
-  for (int j = D - 1; j > 0; --j) suf[j - 1] = suf[j] * (z - float(j));
-  float pre = 1.0f;
+  for (int j = D - 1; j > 0; --j) suf[j - 1] = suf[j] * (z - T(j));
+  T pre = T(1);
 #pragma unroll
   for (int j = 0; j < D; ++j) {
-    l[j] = pre * suf[j] * float(lagrange_den(D, j));
-    pre *= z - float(j);
+    l[j] = pre * suf[j] * T(lagrange_den(D, j));
+    pre *= z - T(j);
   }
 }
 
@@ -274,34 +284,33 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
     job.ms[3 * it + 2] = 0;
   }
   bool done = false;
-  if constexpr (F32) {
-    // 0. (FP32 form) the factorised row: X = a Dh1 + E with E = c2h Dh2 + c3h Dh3
-    //    the same for every point, and the derivative matrices of the window
-    //    commute (they are powers of one differentiation matrix on the local
-    //    polynomial space), so e_r^T exp(X) = e_r^T exp(a Dh1) exp(E) = l(r + a)^T
-    //    exp(E) (Thm. 1 and Thm. 2); exp(E) comes with the launch
-    if (job.sl && live) {
-      float l[D];
-      lagrange_weights<D>(float(hr) + c1f, l);  // r + a = (r - kr) + (a + kr)
-      float bound = 0.0f;
+  // 0. the factorised row: X = a Dh1 + E with E = c2h Dh2 + c3h Dh3 the same for
+  //    every point, and the derivative matrices of the window commute (they are
+  //    powers of one differentiation matrix on the local polynomial space), so
+  //    e_r^T exp(X) = e_r^T exp(a Dh1) exp(E) = l(r + a)^T exp(E) (Thm. 1 and the
+  //    General Exactness theorem); exp(E) comes with the launch
+  if (job.sl && live) {
+    PT l[D];
+    if constexpr (F32) lagrange_weights<D, float>(float(hr) + c1f, l);  // r + a = (r - kr) + (a + kr)
+    else lagrange_weights<D, double>(double(hr) + c1h, l);
+    PT bound = PT(0);
 #pragma unroll
-      for (int j = 0; j < D; ++j) bound = fmaf(fabsf(l[j]), job.slr[j], bound);
-      if (bound <= SL_TAU) {
-        const float e0f = p.c0dt != 0.0 ? float(exp(p.c0dt)) : 1.0f;
-        float acc = 0.0f;
+    for (int j = 0; j < D; ++j) bound = fma(abs(l[j]), sl_entry<PT>(job, D * D + j), bound);
+    if (bound <= PT(SL_TAU)) {
+      const PT e0 = p.c0dt != 0.0 ? PT(exp(p.c0dt)) : PT(1);
+      PT acc = PT(0);
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          float rk = 0.0f;
+      for (int k = 0; k < D; ++k) {
+        PT rk = PT(0);
 #pragma unroll
-          for (int j = 0; j < D; ++j) rk = fmaf(l[j], job.slm[j * D + k], rk);
-          rk *= e0f;
-          if (mode == MODE_FROZEN_STEP) acc = fmaf(rk, float(u[base + grid_index(st + k, p.N, p.bc)]), acc);
-          else if (out) out[it * n + k] = ST(rk);
-        }
-        res = ST(acc);
-        done = true;
-        if (job.ms) job.ms[3 * it] = 2;
+        for (int j = 0; j < D; ++j) rk = fma(l[j], sl_entry<PT>(job, j * D + k), rk);
+        rk *= e0;
+        if (mode == MODE_FROZEN_STEP) acc = fma(rk, PT(u[base + grid_index(st + k, p.N, p.bc)]), acc);
+        else if (out) out[it * n + k] = ST(rk);
       }
+      res = ST(acc);
+      done = true;
+      if (job.ms) job.ms[3 * it] = 2;
     }
   }
   unsigned pade = __ballot_sync(FULL, live && !done);

@@ -152,13 +152,13 @@ def test_harvest_frozen(L, H, precision, n, cfl, nu, method):
     for i in range(1, N - 1):
         want[i] = olmep.point_weights(p, u, i, D)[2][0]
     assert np.all(got[0] == 0) and np.all(got[-1] == 0)
-    if nu <= 1e-6 or precision == "mixed":
+    if precision == "mixed":
         assert weight_err(got[1:-1], want[1:-1]) <= tol(precision)
         return
-    # As-written viscosity: ||X||_1 reaches ~470 (s = 7 squarings) and FP64 Pade
-    # scaling and squaring -- the oracle's included -- is only good to ~1e-11
-    # there.  Where the two differ by more than 1e-12 the exact rows decide: the
-    # GPU must be at least as accurate as the oracle (within 2x).
+    # FP64: the exponential of the rounded local matrix -- the oracle's -- can be off by ~1e-12
+    # (and by ~1e-11 at the as-written viscosity, where ||X||_1 reaches ~470 and s = 7), while
+    # the factorised rows avoid that rounding.  Where the two differ by more than 1e-12 the exact
+    # rows decide: the GPU must be at least as accurate as the oracle (within 2x).
     diff = np.max(np.abs(got - want), axis=1) / np.maximum(np.sum(np.abs(want), axis=1), 1e-300)
     diff[0] = diff[-1] = 0.0
     worst = [int(i) for i in np.argsort(-diff)[:12] if diff[i] > 1e-12]
@@ -288,7 +288,13 @@ def test_frozen_step_full_size_sampled(L, H, precision, n, cfl):
             assert got[i] == 0.0
             continue
         idx, r, w = olmep.point_weights(p, u0, i, D)
-        assert abs(got[i] - w[0] @ u0[idx]) <= tol(precision) * scale, i
+        if abs(got[i] - w[0] @ u0[idx]) <= tol(precision) * scale:
+            continue
+        # FP64: the oracle's exponential of the rounded local matrix can be off by ~2e-12 at
+        # n = 13, CFL 4; the exact rational row decides
+        assert precision == "fp64", i
+        ex = exact_row(n, -p.dt * u0[i] / p.h, p.dt * p.c2 / p.h ** 2, r)
+        assert abs(got[i] - ex @ u0[idx]) <= tol(precision) * scale, i
 
 
 # ------------------------------------------------------------------ batched persistent launch
