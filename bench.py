@@ -56,7 +56,7 @@ P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
 # DRAM bytes (read + write) per launch of the dominant kernels, from one ncu capture of the
 # current kernels (profiles/k_warp_frozen_burgers_N65536_n13_cfl4.md and
 # profiles/k_apply_stream_allen_cahn_batch4096_n9.md); set to None when a kernel changes.
-TRAFFIC_K_WARP_13_FLOAT = 338.176e3 + 1.792e3
+TRAFFIC_K_WARP_13_FLOAT = 338.432e3 + 2.560e3
 TRAFFIC_K_APPLY_STREAM_AC = 253.765632e6 + 196.658688e6
 
 
