@@ -584,13 +584,20 @@ def adj_problem(steps: int, seed: int = 0):
     return wl.burgers(N=ADJ_N, n=ADJ_NS, cfl=ADJ_CFL, nu=NU, steps=steps, seed=seed, departure_centring=True)
 
 
-def adj_flops(n: int, s):
-    """FP64 FLOPs of one reverse point step of the adjoint kernel with s squarings: 32 + 5 s
-    n x n products (powers, the two Frechet directions, U, V and their derivatives, the two
-    L = Y1 + Y2 R), the Gauss-Jordan solve of [Q | P | 4 derivative blocks] (6 n^3 FMAs) and
+def adj_flops(n: int, m, s):
+    """FP64 FLOPs of one reverse step summed over the points, by route (m from lmep_frozen_stats).
+    Factorised rows (m = 2): the Lagrange weights and their derivatives by prefix and suffix
+    products (8 n), the bound (2 n), the three rows l^T exp(E), l'^T exp(E), l^T Dh2 exp(E)
+    (6 n^2) and the two dot products (4 n).  Otherwise the Pade derivatives with s squarings:
+    32 + 5 s n x n products (powers, the two Frechet directions, U, V and their derivatives, the
+    two L = Y1 + Y2 R), the Gauss-Jordan solve of [Q | P | 4 derivative blocks] (6 n^3 FMAs) and
     the two dot products of the harvested rows."""
     import numpy as np
-    return float(np.sum(2.0 * n ** 3 * (32 + 5 * s) + 12.0 * n ** 3 + 4.0 * n))
+    m = np.asarray(m)
+    s = np.asarray(s)
+    pade = 2.0 * n ** 3 * (32 + 5 * s) + 12.0 * n ** 3 + 4.0 * n
+    fact = 6.0 * n * n + 14.0 * n
+    return float(np.sum(np.where(m == 2, fact, pade)))
 
 
 def _oracle_grad(task):
@@ -691,6 +698,7 @@ def adjoint_main(args, rank, world, local_rank, cores):
     scratch = torch.empty(L.lmep_adjoint_scratch_bytes(grid, "mixed"), dtype=torch.uint8, device=dev)
     stats = torch.zeros(ADJ_N * B, 3, dtype=torch.int32, device=dev)
     L.lmep_frozen_stats(solver.handle, grid, op, p.dt, x0, stats, "mixed")
+    m_pts = stats[:, 0].cpu().numpy()
     s_pts = stats[:, 1].cpu().numpy()
     L.lmep_adjoint_step(solver.handle, grid, op, p.dt, x0, lam_next, lam, dnu, scratch, "mixed")
     ka, kb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -701,7 +709,7 @@ def adjoint_main(args, rank, world, local_rank, cores):
     kb.record()
     kb.synchronize()
     adj_ms = ka.elapsed_time(kb) / reps
-    flops = adj_flops(ADJ_NS, s_pts)
+    flops = adj_flops(ADJ_NS, m_pts, s_pts)
     achieved = flops / (adj_ms * 1e-3)
     # e2e: host initial states in (pinned), gradient back to the host
     host_u0 = torch.tensor(u0).pin_memory()
@@ -744,14 +752,17 @@ def adjoint_main(args, rank, world, local_rank, cores):
     line = {"metric": "gradient point-steps/s (forward + reverse)", "value": pts / (total * 1e-3),
             "unit": "point-steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 forward + f64 Frechet", "data": "synthetic", "config": adjoint_config(B, K),
+            "dtype": "f32 forward + f64 derivatives (closed form of the factorised rows; Pade Frechet where "
+                     "the bound is large)", "data": "synthetic", "config": adjoint_config(B, K),
             "forward_ms": t_fwd, "reverse_ms": t_bwd,
             "error": {"vs": "FP64 oracle gradient, one step, 4 instances of N = 4096", "rel": err},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
                          "unit": "TFLOP/s", "frac": achieved / P64_NOMINAL, "traffic": None,
-                         "kernel": f"k_adjoint_points<{ADJ_NS}> + k_adjoint_gather (one reverse step, {B} instances)",
+                         "kernel": f"k_adjoint_fact<{ADJ_NS}> + k_adjoint_points (marked points) + k_adjoint_gather "
+                                   f"(one reverse step, {B} instances)",
                          "avg_launch_ms": adj_ms, "flops_per_launch": flops,
-                         "note": "FP64 FLOPs of adj_flops per launch / CUDA-event time; peak = GB300 nominal FP64"},
+                         "note": "FP64 FLOPs of adj_flops (by route) per step / CUDA-event time; "
+                                 "peak = GB300 nominal FP64"},
             "cpu_baseline": cpu,
             "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "point-steps/s",
                     "h2d_bytes_per_step": 4 * ADJ_N * B, "d2h_bytes_per_step": 4 * ADJ_N * B},

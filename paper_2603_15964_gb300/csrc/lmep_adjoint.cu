@@ -14,10 +14,20 @@
 //   U, V and L_U, L_V,
 //   R = Q^-1 P and L = Q^-1 [(L_U + L_V) + (L_U - L_V) R],
 //   squaring  L <- R L + L R,  R <- R^2.
+// With the exp(E) table of the handle (E = c2h Dh2 + c3h Dh3, the point-
+// independent part of X) the derivatives are taken in closed form instead:
+// the row is w = e^{dt c0} l(z)^T exp(E) with z = r + dt (c1 - fa u_i) / h
+// (the derivative matrices commute, Thm. 1), so
+//   dw/du_i = -dt fa / h e^{dt c0} l'(z)^T exp(E),
+//   dw/dnu  =  dt / h^2  e^{dt c0} l(z)^T Dh2 exp(E),
+// one point per thread (k_adjoint_fact); points whose bound
+// sum_j |l_j| |row j of exp(E)|_1 exceeds 16 are marked and take the Pade
+// derivatives in k_adjoint_points.
 // Everything in this file runs in FP64; lam is stored in the state dtype.
 // The exact re-centring of the forward step (row r of exp(X) equals row r-k
 // of exp(X + k Dh1)) shifts X by a constant matrix, so the directions E are
 // unchanged and the same identity holds for L.
+#include <climits>
 #include <cstdio>
 
 #include "lmep_device.cuh"
@@ -114,11 +124,16 @@ __device__ void gj_multi(double* G, int nb, int lane) {
   }
 }
 
+// Window offset of a point left to k_adjoint_points by k_adjoint_fact.
+constexpr int32_t ADJ_MARK = INT32_MIN;
+
+// Warps take chunks of 32 consecutive points; with fix != 0 only the points
+// that k_adjoint_fact marked (st_out == ADJ_MARK), otherwise every point.
 template <int D, typename ST>
 __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST* __restrict__ u,
                                                             const ST* __restrict__ lam_next, ST* __restrict__ Wout,
                                                             ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
-                                                            double* dnu) {
+                                                            double* dnu, int fix) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -153,7 +168,12 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
                    b1 = pade_b(13, 1), b0 = pade_b(13, 0);
   double dnu_acc = 0.0;
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
-  for (int64_t it = int64_t(blockIdx.x) * AW + warp; it < items; it += int64_t(gridDim.x) * AW) {
+  for (int64_t c = (int64_t(blockIdx.x) * AW + warp) * 32; c < items; c += int64_t(gridDim.x) * AW * 32) {
+   const bool mine = c + lane < items && (!fix || st_out[c + lane] == ADJ_MARK);
+   unsigned todo = __ballot_sync(FULL, mine);
+   while (todo) {
+    const int64_t it = c + (__ffs(todo) - 1);
+    todo &= todo - 1;
     // the squaring phase swaps these scratch roles in place: every point starts from the same layout
     T = Mt(7);
     for (int q = 0; q < 2; ++q) {
@@ -286,16 +306,104 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     const double gu = warp_sum(lane < n ? LU[0][hr * LA + lane] * uj : 0.0);
     const double gn = warp_sum(lane < n ? LU[1][hr * LA + lane] * uj : 0.0);
     if (lane < n) Wout[it * n + lane] = ST(R[hr * LA + lane]);
+    __syncwarp();  // every lane has read this chunk's marks before lane 0 overwrites st_out
     if (lane == 0) {
       gu_out[it] = ST(gu);
       st_out[it] = int32_t(st - i);
       dnu_acc += double(lam_next[it]) * gn;
     }
     __syncwarp();
+   }
   }
   if (lane == 0 && dnu_acc != 0.0) atomicAdd(&dnu_blk, dnu_acc);
   __syncthreads();
   if (threadIdx.x == 0 && dnu_blk != 0.0) atomicAdd(dnu, dnu_blk);
+}
+
+// The factorised tables of one launch, as kernel parameters: exp(E), its
+// absolute row sums and Dh2 exp(E), row-major D x D.
+template <int D>
+struct AdjTables {
+  double ex[D * D];
+  double rs[D];
+  double d2ex[D * D];
+};
+
+// One point per thread: the row w, g_u = dw/du_i . u[window] and the window
+// offset into the scratch arrays of k_adjoint_gather, lam+_i dw/dnu . u[window]
+// into dnu; a point whose bound exceeds the threshold gets st_out = ADJ_MARK.
+template <int D, typename ST>
+__global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTables<D> t, const ST* __restrict__ u,
+                                                      const ST* __restrict__ lam_next, ST* __restrict__ Wout,
+                                                      ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
+                                                      double* dnu) {
+  const int n = p.n;
+  const bool dir = p.bc == BC_DIRICHLET;
+  const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
+  const double e0 = p.c0dt != 0.0 ? exp(p.c0dt) : 1.0;
+  const double su = -p.dt * p.fa / p.h, snu = p.dt / (p.h * p.h);
+  double dnu_acc = 0.0;
+  for (int64_t it = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; it < items;
+       it += int64_t(gridDim.x) * blockDim.x) {
+    int64_t bb, i;
+    split_index(it, p.N, p.batch, bb, i);
+    const ST* ub = u + bb * p.N;
+    if (dir && (i == 0 || i == p.N - 1)) {
+      for (int j = 0; j < n; ++j) Wout[it * n + j] = ST(0);
+      gu_out[it] = ST(0);
+      st_out[it] = 0;
+      continue;
+    }
+    const double ui = double(ub[i]);
+    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
+    const int64_t st = window_start(i, p.N, n, p.bc, k);
+    const double z = double(i - st) + p.dt * (p.c1 - p.fa * ui) / p.h;
+    // Lagrange weights l_j(z) and l_j'(z) by prefix and suffix products carried with
+    // their derivatives (exact at the nodes)
+    double suf[D], sufd[D];
+    suf[D - 1] = 1.0;
+    sufd[D - 1] = 0.0;
+#pragma unroll
+    for (int j = D - 1; j > 0; --j) {
+      sufd[j - 1] = fma(sufd[j], z - double(j), suf[j]);
+      suf[j - 1] = suf[j] * (z - double(j));
+    }
+    double l[D], ld[D];
+    double pre = 1.0, pred = 0.0, bound = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const double c = lagrange_den(D, j);
+      l[j] = pre * suf[j] * c;
+      ld[j] = fma(pred, suf[j], pre * sufd[j]) * c;
+      bound = fma(fabs(l[j]), t.rs[j], bound);
+      pred = fma(pred, z - double(j), pre);
+      pre *= z - double(j);
+    }
+    if (!(bound <= 16.0)) {
+      st_out[it] = ADJ_MARK;
+      continue;
+    }
+    double gu = 0.0, gn = 0.0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      double w = 0.0, wu = 0.0, wn = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        w = fma(l[j], t.ex[j * D + q], w);
+        wu = fma(ld[j], t.ex[j * D + q], wu);
+        wn = fma(l[j], t.d2ex[j * D + q], wn);
+      }
+      const double uq = double(ub[grid_index(st + q, p.N, p.bc)]);
+      Wout[it * n + q] = ST(e0 * w);
+      gu = fma(wu, uq, gu);
+      gn = fma(wn, uq, gn);
+    }
+    gu_out[it] = ST(e0 * su * gu);
+    st_out[it] = int32_t(st - i);
+    dnu_acc = fma(double(lam_next[it]), e0 * snu * gn, dnu_acc);
+  }
+  dnu_acc = warp_sum(dnu_acc);
+  if ((threadIdx.x & 31) == 0 && dnu_acc != 0.0) atomicAdd(dnu, dnu_acc);
 }
 
 // lam[k] = sum over points i whose window holds k of lam+_i w_i[k - start_i] + lam+_k g_u,k
@@ -332,11 +440,25 @@ __global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, con
 
 template <int D, typename ST>
 cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
-                        void* scratch, unsigned* flags, cudaStream_t s) {
+                        void* scratch, unsigned* flags, cudaStream_t s, const double* sl) {
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
   ST* W = static_cast<ST*>(scratch);
   ST* gu = W + items * p.n;
   int32_t* st = reinterpret_cast<int32_t*>(gu + items);
+  int fix = 0;
+  if (sl) {
+    AdjTables<D> t;
+    for (int e = 0; e < D * D; ++e) t.ex[e] = sl[e];
+    for (int j = 0; j < D; ++j) t.rs[j] = sl[D * D + j];
+    for (int e = 0; e < D * D; ++e) t.d2ex[e] = sl[D * D + D + e];
+    int64_t gf = (items + 127) / 128;
+    if (gf > int64_t(device_info().sms) * 16) gf = int64_t(device_info().sms) * 16;
+    k_adjoint_fact<D, ST><<<int(gf), 128, 0, s>>>(p, t, static_cast<const ST*>(u), static_cast<const ST*>(lam_next),
+                                                  W, gu, st, dnu);
+    cudaError_t ef = cudaGetLastError();
+    if (ef != cudaSuccess) return ef;
+    fix = 1;
+  }
   const size_t smem = DHB + AW * AdjWs<D>::BYTES;
   auto k1 = k_adjoint_points<D, ST>;
   cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -345,10 +467,10 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, 32 * AW, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t grid = int64_t(device_info().sms) * per_sm;
-  const int64_t need = (items + AW - 1) / AW;
+  const int64_t need = (items + 32 * AW - 1) / (32 * AW);  // chunks of 32 points per warp
   if (need < grid) grid = need;
   k1<<<int(grid), 32 * AW, smem, s>>>(p, static_cast<const ST*>(u), static_cast<const ST*>(lam_next), W, gu, st,
-                                      dnu);
+                                      dnu, fix);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int blk = 256;
@@ -367,11 +489,11 @@ size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed) {
 }
 
 cudaError_t launch_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
-                           void* scratch, bool mixed, unsigned* flags, cudaStream_t s) {
+                           void* scratch, bool mixed, unsigned* flags, cudaStream_t s, const double* sl) {
 #define ADJ_CASE(DD)                                                                              \
   case DD:                                                                                        \
-    return mixed ? run_adjoint<DD, float>(p, u, lam_next, lam, dnu, scratch, flags, s)            \
-                 : run_adjoint<DD, double>(p, u, lam_next, lam, dnu, scratch, flags, s);
+    return mixed ? run_adjoint<DD, float>(p, u, lam_next, lam, dnu, scratch, flags, s, sl)        \
+                 : run_adjoint<DD, double>(p, u, lam_next, lam, dnu, scratch, flags, s, sl);
   switch (p.n) {
     ADJ_CASE(3)
     ADJ_CASE(5)

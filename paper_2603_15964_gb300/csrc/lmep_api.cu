@@ -30,8 +30,9 @@ struct lmep_handle {
   int device;
   unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
   int32_t expm_method = LMEP_EXPM_AUTO;  // frozen-velocity rows (lmep_set_expm_method)
-  // factorised frozen-velocity rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP64, n x n
-  // then the n absolute row sums), computed once on the device (sl_scratch) and kept on the host
+  // factorised frozen-velocity rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP64, n x n,
+  // the n absolute row sums, then Dh2 exp(E) n x n for the adjoint), computed once on the device
+  // (sl_scratch) and kept on the host
   double* sl_scratch = nullptr;
   std::mutex sl_mu;
   std::map<std::tuple<int, uint64_t, uint64_t>, std::vector<double>> sl_cache;
@@ -116,7 +117,7 @@ uint64_t bits_of(double x) {
 }
 
 // exp(E), E = c2h Dh2 + c3h Dh3, of a frozen operator for the factorised rows (n x n FP64,
-// then the n absolute row sums), from the handle's cache or computed now:
+// the n absolute row sums, then Dh2 exp(E) n x n), from the handle's cache or computed now:
 // one FP64 Pade launch on `stream` and a synchronisation, so only outside a stream
 // capture.  *table = nullptr when it is not available (capture, cache full, non-finite);
 // the rows then take the finite series.
@@ -132,13 +133,15 @@ lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, cons
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   CK(cudaStreamIsCapturing(stream, &cs), "cudaStreamIsCapturing");
   if (cs != cudaStreamCaptureStatusNone || h->sl_cache.size() >= 4096) return LMEP_OK;
-  if (!h->sl_scratch) CK(cudaMalloc(&h->sl_scratch, sizeof(double) * 16 * 16), "cudaMalloc(exp table)");
-  CK(lmep::launch_exp_const(p, h->sl_scratch, stream), "exp(E)");
+  if (!h->sl_scratch) CK(cudaMalloc(&h->sl_scratch, sizeof(double) * 2 * 16 * 16), "cudaMalloc(exp table)");
+  CK(lmep::launch_exp_const(p, h->sl_scratch, h->sl_scratch + 16 * 16, stream), "exp(E)");
   const int n = p.n;
-  std::vector<double> e(size_t(n) * n);
+  std::vector<double> e(size_t(n) * n), d2(size_t(n) * n);
   CK(cudaMemcpyAsync(e.data(), h->sl_scratch, sizeof(double) * n * n, cudaMemcpyDeviceToHost, stream), "read exp(E)");
+  CK(cudaMemcpyAsync(d2.data(), h->sl_scratch + 16 * 16, sizeof(double) * n * n, cudaMemcpyDeviceToHost, stream),
+     "read D2 exp(E)");
   CK(cudaStreamSynchronize(stream), "exp(E)");
-  std::vector<double> t(size_t(n) * n + n);
+  std::vector<double> t(size_t(n) * n + n + size_t(n) * n);
   bool finite = true;
   for (int j = 0; j < n; ++j) {
     double rs = 0.0;
@@ -149,6 +152,10 @@ lmep_status sl_table(lmep_handle* h, const KParams& p, cudaStream_t stream, cons
       rs += std::fabs(v);
     }
     t[size_t(n) * n + j] = rs;
+  }
+  for (size_t q = 0; q < size_t(n) * n; ++q) {
+    finite = finite && std::isfinite(d2[q]);
+    t[size_t(n) * n + n + q] = d2[q];
   }
   if (!finite) t.clear();  // remembered: this operator takes the finite series
   auto ins = h->sl_cache.emplace(key, std::move(t)).first;
@@ -549,8 +556,11 @@ lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_ope
   const bool mixed = precision == LMEP_PREC_MIXED;
   if (scratch_bytes < lmep::adjoint_scratch_bytes(g->N * (g->batch > 1 ? g->batch : 1), g->n, mixed))
     return fail(LMEP_ERR_NOMEM, "scratch too small");
-  CK(lmep::launch_adjoint(make_params(g, op, dt, 0), u_dev, lam_next_dev, lam_dev, dnu_dev, scratch_dev, mixed,
-                          h->flags, S(stream)), "adjoint");
+  const KParams p = make_params(g, op, dt, 0);
+  const double* sl = nullptr;
+  if (h->expm_method == LMEP_EXPM_AUTO && (st = sl_table(h, p, S(stream), &sl)) != LMEP_OK) return st;
+  CK(lmep::launch_adjoint(p, u_dev, lam_next_dev, lam_dev, dnu_dev, scratch_dev, mixed, h->flags, S(stream), sl),
+     "adjoint");
   return LMEP_OK;
 }
 

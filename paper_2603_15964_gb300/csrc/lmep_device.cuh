@@ -46,6 +46,15 @@ __host__ __device__ constexpr double pade_b(int m, int j) {
   return b;
 }
 
+// 1 / prod_{m != j} (j - m): the denominators of the Lagrange basis on the
+// integer nodes 0..n-1.
+__host__ __device__ constexpr double lagrange_den(int n, int j) {
+  double d = 1.0;
+  for (int m = 0; m < n; ++m)
+    if (m != j) d *= double(j - m);
+  return 1.0 / d;
+}
+
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll

@@ -204,9 +204,10 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
 
 // exp(E) of the point-independent part E = c2h Dh2 + c3h Dh3 of a
 // frozen-velocity local matrix: one warp, FP64 Pade scaling and squaring,
-// row-major D x D into out.
+// row-major D x D into out; then Dh2 exp(E) (D x D) into out2, the direction
+// of d exp(E) / d c2h (Dh2 commutes with E).
 template <int D>
-__global__ void __launch_bounds__(32) k_exp_const(KParams p, const double* dh, double* out) {
+__global__ void __launch_bounds__(32) k_exp_const(KParams p, const double* dh, double* out, double* out2) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
   Ws<double> w(smem + DH_BYTES);
@@ -217,22 +218,29 @@ __global__ void __launch_bounds__(32) k_exp_const(KParams p, const double* dh, d
   __syncwarp();
   int m, s;
   warp_expm<D, double>(w, lane, nullptr, 0, true, out, D, &m, &s);
+  __syncwarp();  // orders the global writes of exp(E) before the product below
+  for (int e = lane; e < D * D; e += 32) {
+    const int i = e / D, j = e - (e / D) * D;
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k) acc = fma(Dh[DMAX * LD + i * LD + k], out[k * D + j], acc);
+    out2[e] = acc;
+  }
 }
 
-cudaError_t launch_exp_const(const KParams& p, double* out, cudaStream_t s) {
+cudaError_t launch_exp_const(const KParams& p, double* out, double* out2, cudaStream_t s) {
   const double* d;
   const float* f;
   cudaError_t e = fornberg_of(p.n, &d, &f);
   if (e != cudaSuccess) return e;
   const size_t smem = DH_BYTES + Ws<double>::BYTES;
   switch (p.n) {
-    case 3: k_exp_const<3><<<1, 32, smem, s>>>(p, d, out); break;
-    case 5: k_exp_const<5><<<1, 32, smem, s>>>(p, d, out); break;
-    case 7: k_exp_const<7><<<1, 32, smem, s>>>(p, d, out); break;
-    case 9: k_exp_const<9><<<1, 32, smem, s>>>(p, d, out); break;
-    case 11: k_exp_const<11><<<1, 32, smem, s>>>(p, d, out); break;
-    case 13: k_exp_const<13><<<1, 32, smem, s>>>(p, d, out); break;
-    case 15: k_exp_const<15><<<1, 32, smem, s>>>(p, d, out); break;
+    case 3: k_exp_const<3><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 5: k_exp_const<5><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 7: k_exp_const<7><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 9: k_exp_const<9><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 11: k_exp_const<11><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 13: k_exp_const<13><<<1, 32, smem, s>>>(p, d, out, out2); break;
+    case 15: k_exp_const<15><<<1, 32, smem, s>>>(p, d, out, out2); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -55,8 +55,9 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
 // for the FP32 form).
 cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused, bool mixed,
                           unsigned* flags, cudaStream_t s, int32_t* stats = nullptr, const double* sl = nullptr);
-// exp(c2h Dh2 + c3h Dh3) of the window (FP64, n x n row-major) into out (device).
-cudaError_t launch_exp_const(const KParams& p, double* out, cudaStream_t s);
+// exp(c2h Dh2 + c3h Dh3) of the window (FP64, n x n row-major) into out and
+// Dh2 exp(c2h Dh2 + c3h Dh3) into out2 (device).
+cudaError_t launch_exp_const(const KParams& p, double* out, double* out2, cudaStream_t s);
 
 // ---- banded apply (lmep_apply.cu)
 struct Instance {
@@ -120,8 +121,11 @@ cudaError_t launch_pair_tables(const void* W, int64_t w_stride, int wq, int n, i
 
 // ---- adjoint (lmep_adjoint.cu)
 size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed);
+// sl (host, nullable): the factorised-row table of launch_frozen followed by Dh2 exp(E)
+// (n x n); with it every point whose bound allows takes the factorised derivatives.
 cudaError_t launch_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam,
-                           double* dnu, void* scratch, bool mixed, unsigned* flags, cudaStream_t s);
+                           double* dnu, void* scratch, bool mixed, unsigned* flags, cudaStream_t s,
+                           const double* sl = nullptr);
 
 // ---- peak (lmep_peak.cu)
 cudaError_t fma_peak(bool fp32, double* flops);

@@ -70,15 +70,6 @@ __device__ __forceinline__ PT sl_entry(const WarpJob& job, int e) {
 // exact one.
 constexpr float SL_TAU = 16.0f;
 
-// 1 / prod_{m != j} (j - m): the denominators of the Lagrange basis on the
-// integer nodes 0..n-1.
-__host__ __device__ constexpr double lagrange_den(int n, int j) {
-  double d = 1.0;
-  for (int m = 0; m < n; ++m)
-    if (m != j) d *= double(j - m);
-  return 1.0 / d;
-}
-
 // Row z of the advection exponential on the window: the Lagrange weights l_j(z)
 // of the nodes 0..n-1 (Thm. 1: row r of exp(a Dh1) is l(r + a)), by prefix
 // and suffix products (no division by z - j, exact at the nodes).

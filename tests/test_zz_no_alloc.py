@@ -4,8 +4,9 @@ Callers that cannot allocate device memory (their host application's
 allocator owns the device, or their loop must not enter the driver's
 allocator) use the entry point whose scratch is a static array inside the
 library.  Two calls in a row -- the second reusing the static scratch the
-first left behind -- must each match the allocating entry point within the
-parity tolerance used by the other GPU tests.  This file is collected last
+first left behind -- must each match the allocating entry point (on the same
+route: Pade derivatives) within the parity tolerance used by the other GPU
+tests.  This file is collected last
 and also runs alone in a fresh process.
 """
 import numpy as np
@@ -28,6 +29,9 @@ def L():
 
 
 def reference(L, h, p, u, lam_next, precision):
+    """The allocating entry point on the route the allocation-free one takes: without a handle
+    there is no exp(E) table, so both take the Pade derivatives of every point."""
+    L.lmep_set_expm_method(h, "pade")
     dt_ = L.state_dtype(precision)
     g = grid_of(p)
     scratch = torch.empty(L.lmep_adjoint_scratch_bytes(g, precision), dtype=torch.uint8, device="cuda")
