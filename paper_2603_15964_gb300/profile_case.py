@@ -5,10 +5,12 @@ fused frozen-velocity Burgers step (N = 65536, n = 13, CFL = 4, nu = 1e-6,
 departure-centred) in the FP32 form and one in FP64.  Used with
 `ncu -k regex:k_warp -s 4 -c 2` (the two launches after four warm-up launches).
 
-`python -m paper_2603_15964_gb300.profile_case adj`: one reverse step of the
-frozen-velocity Burgers adjoint (N = 262144, one instance, n = 9, CFL = 2,
-FP32 state, FP64 Frechet derivatives) after one warm-up step.  Used with
-`ncu -k regex:k_adjoint_points -s 1 -c 1`.
+`python -m paper_2603_15964_gb300.profile_case adj [auto|pade]`: one reverse
+step of the frozen-velocity Burgers adjoint (N = 262144, one instance, n = 9,
+CFL = 2, FP32 state, FP64 derivatives: closed form of the factorised rows
+with "auto", Pade Frechet derivatives with "pade") after one warm-up step.
+Used with `ncu -k regex:k_adjoint_fact -s 1 -c 1` ("auto") or
+`ncu -k regex:k_adjoint_points -s 1 -c 1` ("pade").
 
 `python -m paper_2603_15964_gb300.profile_case ac [tile block]`: the batched
 Allen-Cahn ETDRK2 step (4096 instances, N log-uniform in [1024, 65536],
@@ -64,7 +66,7 @@ def allen_cahn(tile: int = 1024, block: int = 128) -> None:
     print("profile case ok")
 
 
-def adjoint() -> None:
+def adjoint(method: str = "auto") -> None:
     import torch
 
     import paper_2603_15964_gb300 as L
@@ -74,6 +76,7 @@ def adjoint() -> None:
     g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True)
     op = L.Operator(c2=p.c2, frozen_adv=1.0)
     h = L.Handle()
+    L.lmep_set_expm_method(h, method)
     u = torch.tensor(wl.burgers_ic(p.N, 0), dtype=torch.float32, device="cuda")
     lam_next = torch.ones_like(u)
     lam = torch.empty_like(u)
@@ -88,7 +91,7 @@ def adjoint() -> None:
 
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "adj":
-        adjoint()
+        adjoint(*sys.argv[2:3])
     elif len(sys.argv) > 1 and sys.argv[1] == "ac":
         allen_cahn(*(int(a) for a in sys.argv[2:]))
     else:
