@@ -51,7 +51,7 @@ typedef enum {
   LMEP_ERR_INVALID = 1,     /* bad argument; nothing was launched */
   LMEP_ERR_CUDA = 2,        /* a CUDA call failed; see lmep_last_error() */
   LMEP_ERR_NONFINITE = 3,   /* a kernel produced Inf/NaN since the last sync */
-  LMEP_ERR_TIMEOUT = 4,     /* reserved: no kernel of this library waits on a flag */
+  LMEP_ERR_TIMEOUT = 4,     /* a kernel gave up a bounded wait for one of its own bulk copies */
   LMEP_ERR_UNSUPPORTED = 5, /* valid request outside the built shapes (e.g. n + n_phi > 16) */
   LMEP_ERR_NOMEM = 6        /* workspace smaller than required */
 } lmep_status;
@@ -194,6 +194,54 @@ LMEP_API lmep_status lmep_step_batched(lmep_handle* h, const void* workspace_dev
 LMEP_API lmep_status lmep_step_batched_once(lmep_handle* h, const void* workspace_dev, const void* u_in_dev,
                                             void* u_out_dev, void* stream);
 
+/* Several frozen-velocity problems advanced together, one persistent
+ * launch per step (Sec. 2.1 steps 1-3 fused with the banded update of
+ * Sec. 3.1 step 3; every point rebuilds and exponentiates its local operator
+ * at every step).  Instance b has its own grid (N, h, boundary, stencil width
+ * n, departure centring), frozen operator and time step.  The row of exp(X)
+ * of a point is l(r + a)^T exp(E) (see lmep_set_expm_method: Thm. 1 with the
+ * General Exactness theorem), exp(E) computed once per instance on the device
+ * by lmep_frozen_set_prepare (or again by lmep_frozen_set_refresh); a point
+ * whose error bound is too large for that form is finished, within the same
+ * call, by the finite series or Pade scaling and squaring, exactly as
+ * lmep_step does for one instance.  The route follows the handle's
+ * lmep_set_expm_method at prepare time (AUTO: factorised rows first; SERIES
+ * or PADE: every point through those stages).
+ *
+ * State layout (u_in, u_out, state dtype of `precision`): the instances back
+ * to back, instance b at element o_b = sum_{c<b} round_up(N_c, 4); the
+ * padding elements are neither read nor written.  Results equal those of
+ * lmep_step with a NULL weight array on each instance, bit for bit. */
+typedef struct lmep_frozen_set_desc {
+  int64_t B;                         /* instances, 1 .. 2^20 */
+  const lmep_grid* grids_host;       /* [B]: odd n 3..15, batch <= 1, N < 2^31 (Neumann: N >= 2n) */
+  const lmep_operator* ops_host;     /* [B]: frozen_adv != 0 */
+  const double* dt_host;             /* [B]: > 0 */
+  int32_t block;                     /* threads per CTA: 0 (default 256), 64, 128, 256 or 512 */
+  int32_t points_per_thread;         /* 0 (default 2), 1 or 2; a CTA updates block * this points */
+} lmep_frozen_set_desc;
+
+/* Bytes of the workspace of a set (instance records, tile table, exp(E)
+ * tables, one int32 per point for the rejected-point lists). */
+LMEP_API lmep_status lmep_frozen_set_workspace_bytes(const lmep_frozen_set_desc* d, int32_t precision,
+                                                     size_t* bytes_out);
+/* Fill a caller-allocated workspace (16-byte aligned, at least
+ * lmep_frozen_set_workspace_bytes bytes) and compute every instance's exp(E)
+ * on the device.  Copies host tables and synchronises `stream`, so it is not
+ * for stream capture.  The workspace then belongs to handle h until it is
+ * prepared again. */
+LMEP_API lmep_status lmep_frozen_set_prepare(lmep_handle* h, const lmep_frozen_set_desc* d, void* workspace_dev,
+                                             size_t workspace_bytes, int32_t precision, void* stream);
+/* Recompute the exp(E) tables of a prepared workspace on the device (one
+ * launch, no host memory touched; the per-run setup cost of the set). */
+LMEP_API lmep_status lmep_frozen_set_refresh(lmep_handle* h, void* workspace_dev, void* stream);
+/* One step of every instance from u_in_dev to u_out_dev (distinct,
+ * non-overlapping buffers): two launches, no host synchronisation, suitable
+ * for replay in a CUDA graph that alternates the two buffers.  Calls that
+ * share a workspace must not overlap on the GPU. */
+LMEP_API lmep_status lmep_frozen_set_step_once(lmep_handle* h, const void* workspace_dev, const void* u_in_dev,
+                                               void* u_out_dev, void* stream);
+
 /* (a7) one reverse step of the frozen-velocity linear scheme (Dirichlet or
  * periodic), given the forward state u^n:
  *   lam_dev[k]  = sum_i lam_next[i] dF_i/du_k,
@@ -218,11 +266,19 @@ LMEP_API lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const
  * every GPU that loads the library until the process exits.  The paper has
  * no counterpart; this is an interface for such callers only.
  *  - Limit: grids needing more than 8 MiB of scratch (N (n + 1) elements of
- *    the state dtype + 4 N + 256 bytes, e.g. N <= 61680 at n = 15 in FP64)
- *    are rejected with LMEP_ERR_INVALID and a message; use lmep_adjoint_step.
+ *    the state dtype + 4 N + 256 bytes, e.g. N <= 63548 at n = 15 in FP64,
+ *    N <= 123358 at n = 15 in the FP32 form) are rejected with
+ *    LMEP_ERR_INVALID and a message; use lmep_adjoint_step.
+ *  - Route: without a handle there is no cached exp(E) table, so every point
+ *    takes the Pade Frechet derivatives (the route lmep_adjoint_step takes
+ *    under LMEP_EXPM_PADE); on the Burgers benchmark grids that is about two
+ *    orders of magnitude slower than the default route of lmep_adjoint_step,
+ *    with the same parity tolerances.
  *  - The first call on each device, with that device current, looks up the
- *    array's device address (cudaGetSymbolAddress) and caches it; make that
- *    first call before any stream capture.
+ *    array's device address (cudaGetSymbolAddress) and caches it; later
+ *    calls check the cached address against the current context (after a
+ *    cudaDeviceReset it is looked up again).  Make the first call on a
+ *    device, and the first after a reset, before any stream capture.
  *  - Every call shares the one array, which keeps the last call's contents;
  *    every scratch element a call reads is written earlier in the same call.
  *    Calls that overlap on the GPU (other streams, other threads) race on it.
@@ -277,6 +333,18 @@ LMEP_API lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const
  * All routes meet the same parity tolerances.  Other calls are unaffected.
  * Returns LMEP_ERR_INVALID for a NULL handle or an unknown method. */
 LMEP_API lmep_status lmep_set_expm_method(lmep_handle* h, int32_t method);
+
+/* Bound of the waits of the streaming apply kernels of handle h (lmep_step
+ * with stored weights on periodic and Neumann grids, lmep_step_batched and
+ * lmep_step_batched_once): a warp waits at most `polls` polls of its tile's
+ * mbarrier for the bulk copies of its next tile; if they have not all landed
+ * it gives up, sets the timeout flag (reported as LMEP_ERR_TIMEOUT by
+ * lmep_sync_status), waits with the default bound for its copies still in
+ * flight and leaves its remaining tiles not computed.  Default (and polls < 0):
+ * 2^20 polls, far longer than any copy; 0 makes every such wait give up at
+ * once -- for tests of the timeout path, which leaves the context usable.
+ * polls > 2^30 is rejected. */
+LMEP_API lmep_status lmep_set_wait_limit(lmep_handle* h, int64_t polls);
 
 /* Synchronise `stream`, read and clear the device status flags.
  * Returns LMEP_ERR_TIMEOUT if a kernel gave up a bounded wait for one of its

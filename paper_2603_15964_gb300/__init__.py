@@ -21,8 +21,9 @@ from ._lib import BC, EXPM, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
 
 __all__ = ["Grid", "Operator", "Handle", "lmep_build_operator", "lmep_expm", "lmep_harvest_weights",
            "lmep_step", "lmep_batch_workspace_bytes", "lmep_batch_prepare", "lmep_step_batched",
-           "lmep_step_batched_once",
-           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_set_expm_method", "lmep_sync_status",
+           "lmep_step_batched_once", "lmep_frozen_set_workspace_bytes", "lmep_frozen_set_prepare",
+           "lmep_frozen_set_refresh", "lmep_frozen_set_step_once", "frozen_set_offsets",
+           "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_set_expm_method", "lmep_set_wait_limit", "lmep_sync_status",
            "lmep_fma_peak",
            "state_dtype", "LmepError"]
 
@@ -158,6 +159,45 @@ def lmep_step_batched_once(h: Handle, workspace, u_in, u_out, stream=None) -> No
     _lib.call("lmep_step_batched_once", h.ptr, _ptr(workspace), _ptr(u_in), _ptr(u_out), _stream(stream))
 
 
+def _set_desc(grids, ops, dts, block=0, points_per_thread=0):
+    B = len(grids)
+    g_arr = (_lib.LmepGrid * B)(*[g.c() for g in grids])
+    o_arr = (_lib.LmepOperator * B)(*[o.c() for o in ops])
+    t_arr = (C.c_double * B)(*[float(t) for t in dts])
+    d = _lib.LmepFrozenSetDesc(B, g_arr, o_arr, t_arr, block, points_per_thread)
+    return d, (g_arr, o_arr, t_arr)
+
+
+def frozen_set_offsets(Ns) -> list:
+    """Start of every instance in a frozen set's state: prefix sums of N_b rounded up to 4."""
+    offs = [0]
+    for v in Ns:
+        offs.append(offs[-1] + (int(v) + 3) // 4 * 4)
+    return offs
+
+
+def lmep_frozen_set_workspace_bytes(grids, ops, dts, precision="mixed", block=0, points_per_thread=0) -> int:
+    d, keep = _set_desc(grids, ops, dts, block, points_per_thread)
+    out = C.c_size_t()
+    _lib.call("lmep_frozen_set_workspace_bytes", C.byref(d), PREC[precision], C.byref(out))
+    return int(out.value)
+
+
+def lmep_frozen_set_prepare(h: Handle, grids, ops, dts, workspace, precision="mixed", block=0, points_per_thread=0,
+                            stream=None) -> None:
+    d, keep = _set_desc(grids, ops, dts, block, points_per_thread)
+    _lib.call("lmep_frozen_set_prepare", h.ptr, C.byref(d), _ptr(workspace),
+              workspace.numel() * workspace.element_size(), PREC[precision], _stream(stream))
+
+
+def lmep_frozen_set_refresh(h: Handle, workspace, stream=None) -> None:
+    _lib.call("lmep_frozen_set_refresh", h.ptr, _ptr(workspace), _stream(stream))
+
+
+def lmep_frozen_set_step_once(h: Handle, workspace, u_in, u_out, stream=None) -> None:
+    _lib.call("lmep_frozen_set_step_once", h.ptr, _ptr(workspace), _ptr(u_in), _ptr(u_out), _stream(stream))
+
+
 def lmep_adjoint_scratch_bytes(grid: Grid, precision: str = "fp64") -> int:
     out = C.c_size_t()
     _lib.call("lmep_adjoint_scratch_bytes", C.byref(grid.c()), PREC[precision], C.byref(out))
@@ -189,6 +229,11 @@ def lmep_set_expm_method(h: Handle, method: str = "auto") -> None:
     matrix, Pade scaling and squaring where its error bound is large), "auto" (the factorised row
     l(r + a)^T exp(E) first, then as "series") or "pade"."""
     _lib.call("lmep_set_expm_method", h.ptr, EXPM[method])
+
+
+def lmep_set_wait_limit(h: Handle, polls: int = -1) -> None:
+    """Bound (in polls) of the streaming apply's waits for its bulk copies; -1 restores the default."""
+    _lib.call("lmep_set_wait_limit", h.ptr, int(polls))
 
 
 def lmep_sync_status(h: Handle, stream=None) -> None:

@@ -40,6 +40,11 @@ class LmepBatchDesc(C.Structure):
                 ("ctas_per_sm", C.c_int32), ("dt", C.c_double), ("op", LmepOperator)]
 
 
+class LmepFrozenSetDesc(C.Structure):
+    _fields_ = [("B", C.c_int64), ("grids_host", C.POINTER(LmepGrid)), ("ops_host", C.POINTER(LmepOperator)),
+                ("dt_host", C.POINTER(C.c_double)), ("block", C.c_int32), ("points_per_thread", C.c_int32)]
+
+
 class LmepError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: status {status} ({detail})")
@@ -61,6 +66,10 @@ _SIGS = {
     "lmep_batch_prepare": [_P, C.POINTER(LmepBatchDesc), _P, C.c_size_t, C.c_int32, _P],
     "lmep_step_batched": [_P, _P, _P, _P, C.c_int64, _P],
     "lmep_step_batched_once": [_P, _P, _P, _P, _P],
+    "lmep_frozen_set_workspace_bytes": [C.POINTER(LmepFrozenSetDesc), C.c_int32, C.POINTER(C.c_size_t)],
+    "lmep_frozen_set_prepare": [_P, C.POINTER(LmepFrozenSetDesc), _P, C.c_size_t, C.c_int32, _P],
+    "lmep_frozen_set_refresh": [_P, _P, _P],
+    "lmep_frozen_set_step_once": [_P, _P, _P, _P, _P],
     "lmep_adjoint_scratch_bytes": [C.POINTER(LmepGrid), C.c_int32, C.POINTER(C.c_size_t)],
     "lmep_adjoint_step": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, _P, _P, _P,
                           C.c_size_t, C.c_int32, _P],
@@ -68,6 +77,7 @@ _SIGS = {
                                   C.c_int32, _P],
     "lmep_frozen_stats": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, _P, _P, C.c_int32, _P],
     "lmep_set_expm_method": [_P, C.c_int32],
+    "lmep_set_wait_limit": [_P, C.c_int64],
     "lmep_sync_status": [_P, _P],
     "lmep_fma_peak": [C.c_int32, C.POINTER(C.c_double)],
     "lmep_status_string": [C.c_int],

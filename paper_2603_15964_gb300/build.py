@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "liblmep.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lmep_expm_f64.cu", "lmep_expm_f32.cu", "lmep_adjoint.cu", "lmep_api.cu", "lmep_expm.cu",
-           "lmep_apply.cu", "lmep_apply_stream.cu", "lmep_peak.cu", "lmep_noalloc.cu"]
+SOURCES = ["lmep_set_fb_f64.cu", "lmep_set_fb_f32.cu", "lmep_expm_f64_hi.cu", "lmep_expm_f32_hi.cu",
+           "lmep_frozen_set.cu", "lmep_expm_f64.cu", "lmep_expm_f32.cu", "lmep_adjoint.cu", "lmep_api.cu",
+           "lmep_expm.cu", "lmep_apply.cu", "lmep_apply_stream.cu", "lmep_peak.cu", "lmep_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]

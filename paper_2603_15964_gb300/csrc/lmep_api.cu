@@ -16,6 +16,7 @@
 using lmep::ApplyParams;
 using lmep::Instance;
 using lmep::KParams;
+using lmep::make_params;
 
 struct BatchPlan {
   ApplyParams ap;
@@ -30,6 +31,7 @@ struct lmep_handle {
   int device;
   unsigned* flags;  // device status word: bit 0 = non-finite output, bit 1 = a bounded wait gave up
   int32_t expm_method = LMEP_EXPM_AUTO;  // frozen-velocity rows (lmep_set_expm_method)
+  int32_t wait_polls = 1 << 20;          // bound of the streaming apply's waits (lmep_set_wait_limit)
   // factorised frozen-velocity rows: exp(E) per (n, c2h, c3h) of a frozen operator (FP64, n x n,
   // the n absolute row sums, then Dh2 exp(E) n x n for the adjoint), computed once on the device
   // (sl_scratch) and kept on the host
@@ -37,6 +39,7 @@ struct lmep_handle {
   std::mutex sl_mu;
   std::map<std::tuple<int, uint64_t, uint64_t>, std::vector<double>> sl_cache;
   std::map<const void*, BatchPlan> plans;
+  std::map<const void*, lmep::SetLayout> sets;  // prepared frozen-velocity sets, by workspace
 };
 
 namespace {
@@ -76,36 +79,6 @@ lmep_status check_prec(int32_t precision) {
   if (precision != LMEP_PREC_FP64 && precision != LMEP_PREC_MIXED)
     return fail(LMEP_ERR_INVALID, "precision must be LMEP_PREC_FP64 or LMEP_PREC_MIXED");
   return LMEP_OK;
-}
-
-KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int n_phi) {
-  KParams p{};
-  p.N = g->N;
-  p.batch = g->batch > 1 ? g->batch : 1;
-  p.h = g->h;
-  p.bc = g->bc;
-  p.n = g->n;
-  p.dep = g->departure_centring ? 1 : 0;
-  p.n_phi = n_phi;
-  p.bc_lo = g->bc_lo;
-  p.bc_hi = g->bc_hi;
-  p.dt = dt;
-  p.c0 = op->c0;
-  p.c1 = op->c1;
-  p.c2 = op->c2;
-  p.c3 = op->c3;
-  p.fa = op->frozen_adv;
-  p.dt_h = dt / g->h;
-  p.c0dt = dt * op->c0;
-  p.c2h = dt * op->c2 / (g->h * g->h);
-  p.c3h = dt * op->c3 / (g->h * g->h * g->h);
-  p.c0dt_f = float(p.c0dt);
-  p.c2h_f = float(p.c2h);
-  p.c3h_f = float(p.c3h);
-  p.c1_f = float(p.c1);
-  p.fa_f = float(p.fa);
-  p.dt_h_f = float(p.dt_h);
-  return p;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -172,6 +145,36 @@ int default_fast_tile(bool mixed) { return mixed ? 1024 : 512; }
 }  // namespace
 
 namespace lmep {
+KParams make_params(const lmep_grid* g, const lmep_operator* op, double dt, int n_phi) {
+  KParams p{};
+  p.N = g->N;
+  p.batch = g->batch > 1 ? g->batch : 1;
+  p.h = g->h;
+  p.bc = g->bc;
+  p.n = g->n;
+  p.dep = g->departure_centring ? 1 : 0;
+  p.n_phi = n_phi;
+  p.bc_lo = g->bc_lo;
+  p.bc_hi = g->bc_hi;
+  p.dt = dt;
+  p.c0 = op->c0;
+  p.c1 = op->c1;
+  p.c2 = op->c2;
+  p.c3 = op->c3;
+  p.fa = op->frozen_adv;
+  p.dt_h = dt / g->h;
+  p.c0dt = dt * op->c0;
+  p.c2h = dt * op->c2 / (g->h * g->h);
+  p.c3h = dt * op->c3 / (g->h * g->h * g->h);
+  p.c0dt_f = float(p.c0dt);
+  p.c2h_f = float(p.c2h);
+  p.c3h_f = float(p.c3h);
+  p.c1_f = float(p.c1);
+  p.fa_f = float(p.fa);
+  p.dt_h_f = float(p.dt_h);
+  return p;
+}
+
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace lmep
 
@@ -350,6 +353,7 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
     if (!lmep::apply_configure(a, mixed, block)) return fail(LMEP_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     const int grid = lmep::apply_grid(a, block, 0, mixed);
     for (int64_t t = 0; t < nsteps; ++t) {
+      a.wait_polls = h->wait_polls;
       CK(lmep::launch_apply(a, cur, nxt, W_dev, mixed, block, grid, h->flags, S(stream)), "step(apply)");
       std::swap(cur, nxt);
     }
@@ -503,10 +507,12 @@ lmep_status lmep_step_batched(lmep_handle* h, const void* ws, void* u_dev, void*
   if (nsteps < 0) return fail(LMEP_ERR_INVALID, "nsteps < 0");
   if (!aligned16(u_dev) || !aligned16(work_dev)) return fail(LMEP_ERR_INVALID, "batched states must be 16-byte aligned");
   const BatchPlan& plan = it->second;
+  ApplyParams ap = plan.ap;
+  ap.wait_polls = h->wait_polls;
   void* cur = u_dev;
   void* nxt = work_dev;
   for (int64_t t = 0; t < nsteps; ++t) {
-    CK(lmep::launch_apply(plan.ap, cur, nxt, plan.W, plan.mixed, plan.block, plan.grid, h->flags, S(stream)),
+    CK(lmep::launch_apply(ap, cur, nxt, plan.W, plan.mixed, plan.block, plan.grid, h->flags, S(stream)),
        "step_batched");
     std::swap(cur, nxt);
   }
@@ -525,9 +531,97 @@ lmep_status lmep_step_batched_once(lmep_handle* h, const void* ws, const void* u
   if (!aligned16(u_in_dev) || !aligned16(u_out_dev))
     return fail(LMEP_ERR_INVALID, "batched states must be 16-byte aligned");
   const BatchPlan& plan = it->second;
-  CK(lmep::launch_apply(plan.ap, u_in_dev, u_out_dev, plan.W, plan.mixed, plan.block, plan.grid, h->flags,
-                        S(stream)),
+  ApplyParams ap = plan.ap;
+  ap.wait_polls = h->wait_polls;
+  CK(lmep::launch_apply(ap, u_in_dev, u_out_dev, plan.W, plan.mixed, plan.block, plan.grid, h->flags, S(stream)),
      "step_batched_once");
+  return LMEP_OK;
+}
+
+// ------------------------------------------------------------------ frozen-velocity sets
+namespace {
+lmep_status set_layout(const lmep_frozen_set_desc* d, int32_t precision, int32_t method, lmep::SetLayout* L,
+                       std::vector<KParams>* ps, std::vector<int32_t>* route, std::vector<int64_t>* offs) {
+  if (!d || d->B <= 0 || !d->grids_host || !d->ops_host || !d->dt_host)
+    return fail(LMEP_ERR_INVALID, "bad frozen-set descriptor");
+  if (d->B > (int64_t(1) << 20)) return fail(LMEP_ERR_INVALID, "too many instances");
+  lmep_status st = check_prec(precision);
+  if (st != LMEP_OK) return st;
+  const int block = d->block > 0 ? d->block : 256;
+  const int ppt = d->points_per_thread > 0 ? d->points_per_thread : 2;
+  if (block != 64 && block != 128 && block != 256 && block != 512)
+    return fail(LMEP_ERR_INVALID, "block must be 64, 128, 256 or 512");
+  if (ppt != 1 && ppt != 2) return fail(LMEP_ERR_INVALID, "points_per_thread must be 1 or 2");
+  std::vector<int32_t> n(size_t(d->B));
+  std::vector<int64_t> N(size_t(d->B));
+  int64_t off = 0;
+  for (int64_t b = 0; b < d->B; ++b) {
+    const lmep_grid* g = d->grids_host + b;
+    const lmep_operator* op = d->ops_host + b;
+    const double dt = d->dt_host[b];
+    if ((st = check_grid(g, 0)) != LMEP_OK) return st;
+    if (g->batch > 1) return fail(LMEP_ERR_INVALID, "frozen-set instances take batch <= 1");
+    if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "frozen-set instances need a frozen operator");
+    if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+    if (g->N >= (int64_t(1) << 31)) return fail(LMEP_ERR_UNSUPPORTED, "frozen-set instances take N < 2^31");
+    if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann needs N >= 2n");
+    KParams p = make_params(g, op, dt, 0);
+    p.series = method != LMEP_EXPM_PADE;
+    if (ps) ps->push_back(p);
+    if (route) route->push_back(method == LMEP_EXPM_AUTO ? 0 : 1);
+    if (offs) offs->push_back(off);
+    n[size_t(b)] = g->n;
+    N[size_t(b)] = g->N;
+    off += (g->N + 3) / 4 * 4;
+  }
+  *L = lmep::frozen_set_layout(d->B, n.data(), N.data(), block, ppt, precision == LMEP_PREC_MIXED);
+  if (L->ntiles >= (int64_t(1) << 31)) return fail(LMEP_ERR_UNSUPPORTED, "too many tiles");
+  return LMEP_OK;
+}
+}  // namespace
+
+lmep_status lmep_frozen_set_workspace_bytes(const lmep_frozen_set_desc* d, int32_t precision, size_t* bytes_out) {
+  if (!bytes_out) return fail(LMEP_ERR_INVALID, "bytes_out is NULL");
+  lmep::SetLayout L;
+  lmep_status st = set_layout(d, precision, LMEP_EXPM_AUTO, &L, nullptr, nullptr, nullptr);
+  if (st != LMEP_OK) return st;
+  *bytes_out = L.total;
+  return LMEP_OK;
+}
+
+lmep_status lmep_frozen_set_prepare(lmep_handle* h, const lmep_frozen_set_desc* d, void* ws, size_t bytes,
+                                    int32_t precision, void* stream) {
+  if (!h || !ws) return fail(LMEP_ERR_INVALID, "NULL handle/workspace");
+  if (!aligned16(ws)) return fail(LMEP_ERR_INVALID, "workspace must be 16-byte aligned");
+  lmep::SetLayout L;
+  std::vector<KParams> ps;
+  std::vector<int32_t> route;
+  std::vector<int64_t> offs;
+  lmep_status st = set_layout(d, precision, h->expm_method, &L, &ps, &route, &offs);
+  if (st != LMEP_OK) return st;
+  if (bytes < L.total) return fail(LMEP_ERR_NOMEM, "workspace smaller than lmep_frozen_set_workspace_bytes");
+  h->sets.erase(ws);
+  CK(lmep::frozen_set_prepare(ws, L, ps.data(), route.data(), offs.data(), S(stream)), "frozen_set_prepare");
+  h->sets[ws] = L;
+  return LMEP_OK;
+}
+
+lmep_status lmep_frozen_set_refresh(lmep_handle* h, void* ws, void* stream) {
+  if (!h || !ws) return fail(LMEP_ERR_INVALID, "NULL argument");
+  auto it = h->sets.find(ws);
+  if (it == h->sets.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
+  CK(lmep::frozen_set_refresh(ws, it->second, S(stream)), "frozen_set_refresh");
+  return LMEP_OK;
+}
+
+lmep_status lmep_frozen_set_step_once(lmep_handle* h, const void* ws, const void* u_in_dev, void* u_out_dev,
+                                      void* stream) {
+  if (!h || !ws || !u_in_dev || !u_out_dev) return fail(LMEP_ERR_INVALID, "NULL argument");
+  if (u_in_dev == u_out_dev) return fail(LMEP_ERR_INVALID, "u_in_dev and u_out_dev must differ");
+  auto it = h->sets.find(ws);
+  if (it == h->sets.end()) return fail(LMEP_ERR_INVALID, "workspace was not prepared with this handle");
+  CK(lmep::frozen_set_step(const_cast<void*>(ws), it->second, u_in_dev, u_out_dev, h->flags, S(stream)),
+     "frozen_set_step_once");
   return LMEP_OK;
 }
 
@@ -588,6 +682,13 @@ lmep_status lmep_set_expm_method(lmep_handle* h, int32_t method) {
   if (method != LMEP_EXPM_AUTO && method != LMEP_EXPM_PADE && method != LMEP_EXPM_SERIES)
     return fail(LMEP_ERR_INVALID, "method must be LMEP_EXPM_AUTO, LMEP_EXPM_PADE or LMEP_EXPM_SERIES");
   h->expm_method = method;
+  return LMEP_OK;
+}
+
+lmep_status lmep_set_wait_limit(lmep_handle* h, int64_t polls) {
+  if (!h) return fail(LMEP_ERR_INVALID, "handle is NULL");
+  if (polls > (int64_t(1) << 30)) return fail(LMEP_ERR_INVALID, "polls must be <= 2^30");
+  h->wait_polls = polls < 0 ? (1 << 20) : int32_t(polls);
   return LMEP_OK;
 }
 

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(512) k_apply_stream(ApplyParams a, const ST* _
       if (ftile + nwarps < a.ntiles) dnext = load_desc(a, ftile + nwarps);
     }
     int ok = 1;
-    if (lane == 0) ok = mbar_wait(&bar[s], (parity >> s) & 1u) ? 1 : 0;
+    if (lane == 0) ok = mbar_wait(&bar[s], (parity >> s) & 1u, a.wait_polls) ? 1 : 0;
     ok = __shfl_sync(0xffffffffu, ok, 0);
     __syncwarp();
     if (!ok) {
@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(512) k_apply_stream(ApplyParams a, const ST* _
   }
   if (abort && lane == 0) {
     // a bulk copy did not complete in time: report it and give the copies
-    // still in flight (this tile and the next NS - 1) a bounded time to land
+    // still in flight (this tile and the next NS - 1) the default bounded
+    // time to land, so that none writes into shared memory after the warp
+    // has left
     atomicOr(flags, 2u);
     for (int d = 0; d < NS; ++d) {
       const int j = (s + d) % NS;

@@ -81,7 +81,7 @@ cudaError_t fornberg_init() {
   return e;
 }
 
-static cudaError_t fornberg_of(int n, const double** d, const float** f) {
+cudaError_t fornberg_of(int n, const double** d, const float** f) {
   cudaError_t e = fornberg_init();
   if (e != cudaSuccess) return e;
   int dev = 0;
@@ -211,20 +211,7 @@ __global__ void __launch_bounds__(32) k_exp_const(KParams p, const double* dh, d
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
   Ws<double> w(smem + DH_BYTES);
-  const int lane = threadIdx.x;
-  for (int e = lane; e < 3 * DMAX * LD; e += 32) Dh[e] = dh[e];
-  __syncwarp();
-  assemble<D>(w.X64, Dh, p.n, 0.0, 0.0, p.c2h, p.c3h, lane);
-  __syncwarp();
-  int m, s;
-  warp_expm<D, double>(w, lane, nullptr, 0, true, out, D, &m, &s);
-  __syncwarp();  // orders the global writes of exp(E) before the product below
-  for (int e = lane; e < D * D; e += 32) {
-    const int i = e / D, j = e - (e / D) * D;
-    double acc = 0.0;
-    for (int k = 0; k < D; ++k) acc = fma(Dh[DMAX * LD + i * LD + k], out[k * D + j], acc);
-    out2[e] = acc;
-  }
+  exp_const_warp<D>(p, dh, Dh, w, out, out2, threadIdx.x);
 }
 
 cudaError_t launch_exp_const(const KParams& p, double* out, double* out2, cudaStream_t s) {

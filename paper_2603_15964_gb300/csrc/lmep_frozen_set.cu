@@ -1,0 +1,239 @@
+// lmep_frozen_set.cu -- several frozen-velocity instances, one launch per step.
+//
+// Each instance has its own grid (N, h, boundary), stencil width n, operator
+// and dt; every point rebuilds its local matrix X = a Dh1 + E at every step
+// (Sec. 2.1 steps 1-3, a1-a6 fused).  Its row of exp(X) is taken from the
+// factorisation row_r exp(X) = l(r + a)^T exp(E) (Thm. 1 with the General
+// Exactness theorem: the derivative matrices of the window commute, and row r
+// of exp(a Dh1) is the semi-Lagrangian interpolation at the departure point):
+// the Lagrange weights of the window at the departure point times exp(E), which
+// is the same for every point of an instance.  One step is two launches:
+//
+//   k_frozen_set           one CTA per tile of one instance (tiles of the widest
+//                          stencils first), the tile's values and the instance's
+//                          exp(E) table staged in shared memory, one thread per
+//                          point (or two points sharing the table reads); a
+//                          point whose error bound sum_j |l_j| R_j (R_j the
+//                          absolute row sums of exp(E)) exceeds the bound of the
+//                          factorised route is appended to its instance's list;
+//   k_frozen_set_fallback  the listed points through the finite series of the
+//                          nilpotent local matrix, then Pade scaling and
+//                          squaring (one warp per 32 points, as in k_warp); it
+//                          exits at once when no point was listed, and its last
+//                          CTA clears the lists' counters for the next step.
+//
+// The lean kernel carries only the factorised route, so it needs no Pade
+// workspace and few registers; the lists move the rare rejected points to the
+// fallback without a host round trip, so a step can be replayed from a CUDA
+// graph.  The exp(E) tables are computed on the device (k_frozen_set_setup,
+// FP64 Pade, one warp per instance) with the same arithmetic as the
+// single-instance path, so both give the same bits.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lmep_frozen_set.cuh"
+
+namespace lmep {
+
+namespace {
+// exp(E) table of instance blockIdx.x: FP64 Pade (exp_const_warp, the
+// arithmetic of the single-instance path) into exps, then in the product type
+// its rows (stride NP) and absolute row sums; ok = 0 when exp(E) or Dh2 exp(E)
+// is not finite (the instance then takes the fallback for every point).
+template <int D, typename PT>
+__device__ __forceinline__ void setup_one(const WarpJob& job, const SetInst& in, double* Dh, const Ws<double>& w,
+                                          double* e, PT* tab, int32_t* ok, int lane) {
+  constexpr int NP = tab_np(D);
+  exp_const_warp<D>(job.p, job.dh, Dh, w, e, e + DMAX * DMAX, lane);
+  bool finite = true;
+  for (int q = lane; q < D * D; q += 32) finite = finite && isfinite(e[q]) && isfinite(e[DMAX * DMAX + q]);
+  PT* t = tab + in.tab;
+  if (lane < D) {
+    double rs = 0.0;
+    for (int k = 0; k < NP; ++k) {
+      const double v = k < D ? e[lane * D + k] : 0.0;
+      t[lane * NP + k] = PT(v);
+      if (k < D) rs += fabs(v);
+    }
+    t[D * NP + lane] = PT(rs);
+  } else if (lane < NP) {
+    t[D * NP + lane] = PT(0);
+  }
+  finite = __all_sync(FULL, finite);
+  if (lane == 0) ok[blockIdx.x] = finite ? 1 : 0;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(32) k_frozen_set_setup(const WarpJob* jobs, const SetInst* inst, double* exps,
+                                                         void* tab, int32_t* ok) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double* Dh = reinterpret_cast<double*>(smem);
+  Ws<double> w(smem + DH_BYTES);
+  const int b = blockIdx.x, lane = threadIdx.x;
+  const WarpJob& job = jobs[b];
+  double* e = exps + int64_t(b) * 2 * DMAX * DMAX;
+  PT* t = static_cast<PT*>(tab);
+  switch (job.p.n) {
+    case 3: setup_one<3, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    case 5: setup_one<5, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    case 7: setup_one<7, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    case 9: setup_one<9, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    case 11: setup_one<11, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    case 13: setup_one<13, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+    default: setup_one<15, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+}  // namespace
+
+SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int block, int ppt, bool mixed) {
+  SetLayout L{};
+  const size_t es = mixed ? 4 : 8;
+  const int64_t tp = int64_t(block) * ppt;
+  int64_t tiles = 0, points = 0, tabn = 0;
+  for (int64_t b = 0; b < B; ++b) {
+    tiles += (N[b] + tp - 1) / tp;
+    points += N[b];
+    tabn += tab_elems(n[b]);
+  }
+  L.B = B;
+  L.ntiles = tiles;
+  L.points = points;
+  L.block = block;
+  L.ppt = ppt;
+  L.mixed = mixed;
+  L.ctl = 0;
+  L.ok = align256(L.ctl + size_t(B + 1) * 4);
+  L.inst = align256(L.ok + size_t(B) * 4);
+  L.jobs = align256(L.inst + size_t(B) * sizeof(SetInst));
+  L.tiles = align256(L.jobs + size_t(B) * sizeof(WarpJob));
+  L.exps = align256(L.tiles + size_t(tiles) * sizeof(int2));
+  L.tab = align256(L.exps + size_t(B) * 2 * DMAX * DMAX * 8);
+  L.lists = align256(L.tab + size_t(tabn) * es);
+  L.total = align256(L.lists + size_t(points) * 4);
+  return L;
+}
+
+cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, const int32_t* route,
+                               const int64_t* offsets, cudaStream_t s) {
+  char* base = static_cast<char*>(ws);
+  std::vector<SetInst> inst(size_t(L.B));
+  std::vector<WarpJob> jobs(size_t(L.B));
+  std::vector<int2> tiles;
+  tiles.reserve(size_t(L.ntiles));
+  int64_t list_off = 0, tab = 0;
+  const int64_t tp = int64_t(L.block) * L.ppt;
+  for (int64_t b = 0; b < L.B; ++b) {
+    SetInst& in = inst[size_t(b)];
+    std::memset(&in, 0, sizeof in);
+    in.p = p[b];
+    in.off = offsets[b];
+    in.list_off = list_off;
+    in.tab = tab;
+    in.route = route[b];
+    list_off += p[b].N;
+    tab += tab_elems(p[b].n);
+    WarpJob& j = jobs[size_t(b)];
+    std::memset(&j, 0, sizeof j);
+    j.mode = MODE_FROZEN_STEP;
+    j.p = p[b];
+    j.items = p[b].N;
+    cudaError_t e = fornberg_of(p[b].n, &j.dh, &j.dhf);
+    if (e != cudaSuccess) return e;
+  }
+  // tiles of the widest stencils first: the costliest CTAs start in the first wave
+  std::vector<int64_t> order(size_t(L.B));
+  for (int64_t b = 0; b < L.B; ++b) order[size_t(b)] = b;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return p[x].n > p[y].n; });
+  for (int64_t b : order)
+    for (int64_t t0 = 0; t0 < p[b].N; t0 += tp) tiles.push_back(make_int2(int(b), int(t0)));
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(base + L.ctl, 0, size_t(L.B + 1) * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(base + L.inst, inst.data(), inst.size() * sizeof(SetInst), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(base + L.jobs, jobs.data(), jobs.size() * sizeof(WarpJob), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = frozen_set_refresh(ws, L, s)) != cudaSuccess) return e;
+  // the host copies above read pageable vectors: make sure they are consumed
+  return cudaStreamSynchronize(s);
+}
+
+cudaError_t frozen_set_refresh(void* ws, const SetLayout& L, cudaStream_t s) {
+  char* base = static_cast<char*>(ws);
+  const size_t smem = DH_BYTES + Ws<double>::BYTES;
+  const WarpJob* jobs = reinterpret_cast<const WarpJob*>(base + L.jobs);
+  const SetInst* inst = reinterpret_cast<const SetInst*>(base + L.inst);
+  double* exps = reinterpret_cast<double*>(base + L.exps);
+  int32_t* ok = reinterpret_cast<int32_t*>(base + L.ok);
+  if (L.mixed) {
+    cudaError_t e = allow_smem(k_frozen_set_setup<float>, smem);
+    if (e != cudaSuccess) return e;
+    k_frozen_set_setup<float><<<unsigned(L.B), 32, smem, s>>>(jobs, inst, exps, base + L.tab, ok);
+  } else {
+    cudaError_t e = allow_smem(k_frozen_set_setup<double>, smem);
+    if (e != cudaSuccess) return e;
+    k_frozen_set_setup<double><<<unsigned(L.B), 32, smem, s>>>(jobs, inst, exps, base + L.tab, ok);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+template <typename PT>
+cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_out, unsigned* flags, cudaStream_t s) {
+  SetArgs a;
+  a.inst = reinterpret_cast<const SetInst*>(base + L.inst);
+  a.tiles = reinterpret_cast<const int2*>(base + L.tiles);
+  a.tab = base + L.tab;
+  a.ok = reinterpret_cast<const int32_t*>(base + L.ok);
+  a.fail_count = reinterpret_cast<int32_t*>(base + L.ctl);
+  a.fail_list = reinterpret_cast<int32_t*>(base + L.lists);
+  a.u = u_in;
+  a.out = u_out;
+  a.flags = flags;
+  const size_t smem = (size_t(TAB_MAX) + size_t(L.block) * L.ppt + 2 * DMAX) * sizeof(PT);
+  cudaError_t e;
+  if (L.ppt == 2) {
+    if ((e = allow_smem(k_frozen_set<PT, 2>, smem)) != cudaSuccess) return e;
+    k_frozen_set<PT, 2><<<unsigned(L.ntiles), L.block, smem, s>>>(a);
+  } else {
+    if ((e = allow_smem(k_frozen_set<PT, 1>, smem)) != cudaSuccess) return e;
+    k_frozen_set<PT, 1><<<unsigned(L.ntiles), L.block, smem, s>>>(a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  FbArgs f;
+  f.inst = a.inst;
+  f.jobs = reinterpret_cast<const WarpJob*>(base + L.jobs);
+  f.fail_count = a.fail_count;
+  f.fail_list = a.fail_list;
+  f.done = reinterpret_cast<unsigned*>(base + L.ctl) + L.B;
+  f.B = L.B;
+  f.u = u_in;
+  f.out = u_out;
+  f.flags = flags;
+  const unsigned grid = unsigned(device_info().sms);
+  return sizeof(PT) == 4 ? launch_set_fallback_f32(f, grid, s) : launch_set_fallback_f64(f, grid, s);
+}
+}  // namespace
+
+cudaError_t frozen_set_step(void* ws, const SetLayout& L, const void* u_in, void* u_out, unsigned* flags,
+                            cudaStream_t s) {
+  char* base = static_cast<char*>(ws);
+  return L.mixed ? set_step<float>(base, L, u_in, u_out, flags, s) : set_step<double>(base, L, u_in, u_out, flags, s);
+}
+
+}  // namespace lmep

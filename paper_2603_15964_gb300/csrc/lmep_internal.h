@@ -6,6 +6,9 @@
 #include <string>
 #include <cuda_runtime.h>
 
+struct lmep_grid;
+struct lmep_operator;
+
 namespace lmep {
 
 // Problem parameters passed by value to every kernel.
@@ -33,6 +36,12 @@ struct KParams {
 // Set the thread-local text returned by lmep_last_error().
 void set_last_error(const std::string& msg);
 
+// Kernel parameters of one grid, operator and time step (lmep_api.cu): the
+// derived constants dt/h, dt c0, dt c2/h^2, dt c3/h^3 and their FP32
+// roundings are formed here once, so every entry point passes identical
+// parameters to the kernels.
+KParams make_params(const struct ::lmep_grid* g, const struct ::lmep_operator* op, double dt, int n_phi);
+
 struct DeviceInfo {
   int sms;
   int smem_optin;  // dynamic shared memory a CTA may opt in to (bytes)
@@ -42,6 +51,8 @@ DeviceInfo device_info();
 // ---- expm family (lmep_expm.cu)
 // Build the per-n derivative tables on the current device (once; synchronous).
 cudaError_t fornberg_init();
+// Device addresses of the h^k D^(k) tables (k = 1..3) of width n, FP64 and FP32.
+cudaError_t fornberg_of(int n, const double** d, const float** f);
 cudaError_t launch_build_operator(const KParams& p, const double* u, int64_t i0, int64_t count,
                                   double* M, int32_t* start, int32_t* row, cudaStream_t s);
 cudaError_t launch_expm(const double* A, int64_t P, int d, double* E, bool mixed, int32_t* ms,
@@ -58,6 +69,30 @@ cudaError_t launch_frozen(const KParams& p, const void* u, void* out, bool fused
 // exp(c2h Dh2 + c3h Dh3) of the window (FP64, n x n row-major) into out and
 // Dh2 exp(c2h Dh2 + c3h Dh3) into out2 (device).
 cudaError_t launch_exp_const(const KParams& p, double* out, double* out2, cudaStream_t s);
+
+// ---- frozen-velocity sets (lmep_frozen_set.cu): several instances, each with
+// its own grid, operator, dt and stencil width, advanced by one launch per
+// step (plus a launch that finishes the rare points the first one rejects).
+struct SetLayout {
+  size_t ctl, ok, inst, jobs, tiles, exps, tab, lists, total;  // byte offsets of the regions, total size
+  int64_t B, ntiles, points;
+  int block, ppt;
+  bool mixed;
+};
+// Region offsets and sizes of a set of B instances (widths n[b], sizes N[b]) for
+// tiles of block * ppt points.
+SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int block, int ppt, bool mixed);
+// Fill a workspace: instance records, fallback jobs, tile table (heaviest
+// width first), cleared counters, then the exp(E) tables on the device.
+// route[b] = 0: factorised rows first; 1: every point through the fallback
+// (finite series, then Pade; p.series = 0: Pade only).  Synchronises s.
+cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, const int32_t* route,
+                               const int64_t* offsets, cudaStream_t s);
+// Recompute the exp(E) tables of a prepared workspace (device only).
+cudaError_t frozen_set_refresh(void* ws, const SetLayout& L, cudaStream_t s);
+// One step of every instance from u_in to u_out.
+cudaError_t frozen_set_step(void* ws, const SetLayout& L, const void* u_in, void* u_out, unsigned* flags,
+                            cudaStream_t s);
 
 // ---- banded apply (lmep_apply.cu)
 struct Instance {
@@ -82,6 +117,7 @@ struct ApplyParams {
   int halo;          // staged halo per side (apply_halo / apply_fast_halo)
   int fast;          // 1: pipelined register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
   int stages;        // fast kernel: stage slots per warp (set by apply_configure)
+  int wait_polls;    // fast kernel: bound of a warp's wait for its next tile, in polls (default 2^20)
   int warp_smem;     // fast kernel: shared-memory bytes per warp (set by apply_configure)
   double dt;
   double bc_lo, bc_hi;

@@ -11,7 +11,10 @@
 // In host code the array's name is only a host-side stand-in, not a device
 // address, so the first call on each device (with that device current) asks
 // the runtime for the array's device address with cudaGetSymbolAddress and
-// caches it; later calls reuse the cached address.
+// caches it.  Later calls reuse the cached address after checking that the
+// current context still knows it as device memory of this device (a
+// cudaDeviceReset destroys the context that held it; the next call then looks
+// the address up again in the new one).
 #include <mutex>
 #include <string>
 
@@ -70,6 +73,14 @@ extern "C" lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_
   DeviceAddresses a;
   {
     std::lock_guard<std::mutex> lock(g_mutex);
+    if (g_addr[dev].ready) {
+      cudaPointerAttributes at{};
+      const cudaError_t q = cudaPointerGetAttributes(&at, g_addr[dev].scratch);
+      if (q != cudaSuccess) (void)cudaGetLastError();  // a stale address is not an error of this call
+      if (q != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != dev ||
+          at.devicePointer != g_addr[dev].scratch)
+        g_addr[dev] = DeviceAddresses{};
+    }
     if (!g_addr[dev].ready) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_adjoint_scratch);
@@ -85,25 +96,7 @@ extern "C" lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_
     }
     a = g_addr[dev];
   }
-  lmep::KParams p{};
-  p.N = g->N;
-  p.h = g->h;
-  p.bc = g->bc;
-  p.n = g->n;
-  p.dep = g->departure_centring ? 1 : 0;
-  p.n_phi = 0;
-  p.bc_lo = g->bc_lo;
-  p.bc_hi = g->bc_hi;
-  p.dt = dt;
-  p.c0 = op->c0;
-  p.c1 = op->c1;
-  p.c2 = op->c2;
-  p.c3 = op->c3;
-  p.fa = op->frozen_adv;
-  p.dt_h = dt / g->h;
-  p.c0dt = dt * op->c0;
-  p.c2h = dt * op->c2 / (g->h * g->h);
-  p.c3h = dt * op->c3 / (g->h * g->h * g->h);
+  const lmep::KParams p = lmep::make_params(g, op, dt, 0);
   e = lmep::launch_adjoint(p, u_dev, lam_next_dev, lam_dev, dnu_dev, a.scratch, mixed, a.flags,
                            static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return reject(LMEP_ERR_CUDA, std::string("adjoint(noalloc): ") + cudaGetErrorString(e));

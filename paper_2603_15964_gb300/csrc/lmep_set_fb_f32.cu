@@ -1,0 +1,15 @@
+// lmep_set_fb_f32.cu -- the fallback kernel of the frozen-velocity sets in
+// the FP32 form (finite series, then Pade scaling and squaring, for the
+// points the factorised-row kernel rejected).
+#include "lmep_frozen_set.cuh"
+
+namespace lmep {
+cudaError_t launch_set_fallback_f32(const FbArgs& a, unsigned grid, cudaStream_t s) {
+  const size_t smem = WARPS * Ws<float>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_frozen_set_fallback<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem));
+  if (e != cudaSuccess) return e;
+  k_frozen_set_fallback<float><<<grid, 32 * WARPS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+}  // namespace lmep

@@ -114,11 +114,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// Wait for the phase with the given parity to complete; gives up after a
-// bounded number of polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Default bound of a wait, in polls (far longer than any bulk copy of a tile).
+constexpr int WAIT_POLLS = 1 << 20;
+// Wait for the phase with the given parity to complete; gives up after
+// `polls` polls and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int polls = WAIT_POLLS) {
   const unsigned addr = smem_u32(bar);
-  for (int it = 0; it < (1 << 20); ++it) {
+  for (int it = 0; it < polls; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"

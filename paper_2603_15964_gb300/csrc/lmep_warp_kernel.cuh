@@ -156,17 +156,15 @@ struct SeriesBuf {
 // are returned.  The per-point values hr, c1h, c1f, st and base live in the
 // point's own lane.
 template <int D, typename QT, typename ST>
-__device__ __forceinline__ unsigned series_points(const WarpJob& job, const double* Dh, const float* Dhf,
-                                                  unsigned todo, int lane, int hr, double c1h, float c1f,
-                                                  int64_t st, int64_t base, QT* vb, float* wb, float tau, QT e0,
-                                                  int64_t c, int mcode, ST& res) {
+__device__ __forceinline__ unsigned series_points(const WarpJob& job, const ST* u, ST* out, const double* Dh,
+                                                  const float* Dhf, unsigned todo, int lane, int hr, double c1h,
+                                                  float c1f, int64_t st, int64_t base, QT* vb, float* wb, float tau,
+                                                  QT e0, int64_t c, int mcode, ST& res) {
   constexpr int GS = Groups<D>::GS, G = Groups<D>::G;
   using SB = SeriesBuf<D, QT>;
   const KParams& p = job.p;
   const int n = p.n;
   const int mode = job.mode;
-  const ST* u = static_cast<const ST*>(job.u);
-  ST* out = static_cast<ST*>(job.out);
   const int g = lane / GS, j = lane % GS;
   QT* vg = vb + g * SB::VS;
   float* wg = wb + g * GS;
@@ -224,20 +222,21 @@ __device__ __forceinline__ unsigned series_points(const WarpJob& job, const doub
 //   3. Pade scaling and squaring on the whole warp, one point at a time, for
 //      the rest (every point when p.series == 0).
 // Each result returns to its point's lane and the chunk leaves in one
-// coalesced store.
+// coalesced store.  u and out are the state and the output of the job's
+// instance; with a point list (the rejected points of a frozen set, see
+// lmep_frozen_set.cu) lane l takes point list[c + l] instead of c + l.
 template <int D, typename PT>
 __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w, const double* Dh,
-                                             const float* Dhf, int64_t c, int64_t end, int lane, unsigned& bad) {
+                                             const float* Dhf, int64_t c, int64_t end, int lane, unsigned& bad,
+                                             const PT* u, PT* out, const int32_t* list = nullptr) {
   using ST = PT;
   constexpr bool F32 = sizeof(PT) == 4;
   const KParams& p = job.p;
   const int n = p.n;
   const int mode = job.mode;
-  const ST* u = static_cast<const ST*>(job.u);
-  ST* out = static_cast<ST*>(job.out);
   // ---- lane-parallel preparation of point c + lane
-  const int64_t it = c + lane;
-  const bool valid = it < end;
+  const bool valid = c + lane < end;
+  const int64_t it = list ? (valid ? int64_t(list[c + lane]) : 0) : c + lane;
   int64_t b = 0, i = 0;
   if (valid) split_index(it, p.N, p.batch, b, i);
   const bool wall = valid && p.bc == BC_DIRICHLET && (i == 0 || i == p.N - 1);
@@ -310,14 +309,14 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
     const double e0 = p.c0dt != 0.0 ? exp(p.c0dt) : 1.0;
     PT* vb = w.M(4);  // broadcast buffers in the Pade workspace, which the series does not use
     float* wb = reinterpret_cast<float*>(vb + 2 * SeriesBuf<D, PT>::VPP);
-    pade = series_points<D, PT, ST>(job, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vb, wb,
+    pade = series_points<D, PT, ST>(job, u, out, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vb, wb,
                                     F32 ? SERIES_TAU_F32 : SERIES_TAU_F64, PT(e0), c, 0, res);
     if constexpr (F32) {
       if (pade) {
         c1h = double(c1f);
         double* vd = reinterpret_cast<double*>(w.M(4));
         float* wd = reinterpret_cast<float*>(vd + 2 * SeriesBuf<D, double>::VPP);
-        pade = series_points<D, double, ST>(job, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vd, wd,
+        pade = series_points<D, double, ST>(job, u, out, Dh, Dhf, pade, lane, hr, c1h, c1f, st, base, vd, wd,
                                             SERIES_TAU_F32_FORM_F64, e0, c, 1, res);
       }
     }
@@ -400,7 +399,8 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
     const int64_t end = begin + job.span < job.items ? begin + job.span : job.items;
     const int64_t csz = (job.span + (job.span + 31) / 32 - 1) / ((job.span + 31) / 32);
     for (int64_t c = begin; c < end; c += csz)
-      frozen_chunk<D, PT>(job, w, Dh, Dhf, c, c + csz < end ? c + csz : end, lane, bad);
+      frozen_chunk<D, PT>(job, w, Dh, Dhf, c, c + csz < end ? c + csz : end, lane, bad,
+                          static_cast<const PT*>(job.u), static_cast<PT*>(job.out));
     if (bad) atomicOr(job.flags, 1u);
     return;
   }
@@ -450,6 +450,30 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
   if (bad) atomicOr(job.flags, 1u);
 }
 
+// exp(E) of the point-independent part E = c2h Dh2 + c3h Dh3 of a
+// frozen-velocity local matrix, computed by one warp (FP64 Pade scaling and
+// squaring) into out (D x D row-major, global), then Dh2 exp(E) into out2:
+// the direction of d exp(E) / d c2h (Dh2 commutes with E).  Dh is the
+// warp's shared copy of the derivative tables, filled here from dh.
+template <int D>
+__device__ __forceinline__ void exp_const_warp(const KParams& p, const double* dh, double* Dh, const Ws<double>& w,
+                                               double* out, double* out2, int lane) {
+  for (int e = lane; e < 3 * DMAX * LD; e += 32) Dh[e] = dh[e];
+  __syncwarp();
+  assemble<D>(w.X64, Dh, p.n, 0.0, 0.0, p.c2h, p.c3h, lane);
+  __syncwarp();
+  int m, s;
+  warp_expm<D, double>(w, lane, nullptr, 0, true, out, D, &m, &s);
+  __syncwarp();  // orders the global writes of exp(E) before the product below
+  for (int e = lane; e < D * D; e += 32) {
+    const int i = e / D, j = e - (e / D) * D;
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k) acc = fma(Dh[DMAX * LD + i * LD + k], out[k * D + j], acc);
+    out2[e] = acc;
+  }
+  __syncwarp();
+}
+
 // Resident CTAs per SM of k_warp<D, PT>, set up once per device (the shared
 // memory attribute and the occupancy query are host calls worth skipping on
 // every launch); 0 on failure, with the error in *err.
@@ -497,8 +521,10 @@ cudaError_t run_warp(const WarpJob& job_in, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The instantiations are split by width over two translation units per
+// product type (d <= 9 and d >= 10), which keeps every unit's compile time short.
 template <typename PT>
-cudaError_t dispatch_warp(int d, const WarpJob& job, cudaStream_t s) {
+cudaError_t dispatch_warp_lo(int d, const WarpJob& job, cudaStream_t s) {
   switch (d) {
     case 3: return run_warp<3, PT>(job, s);
     case 4: return run_warp<4, PT>(job, s);
@@ -507,6 +533,12 @@ cudaError_t dispatch_warp(int d, const WarpJob& job, cudaStream_t s) {
     case 7: return run_warp<7, PT>(job, s);
     case 8: return run_warp<8, PT>(job, s);
     case 9: return run_warp<9, PT>(job, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename PT>
+cudaError_t dispatch_warp_hi(int d, const WarpJob& job, cudaStream_t s) {
+  switch (d) {
     case 10: return run_warp<10, PT>(job, s);
     case 11: return run_warp<11, PT>(job, s);
     case 12: return run_warp<12, PT>(job, s);
@@ -518,6 +550,8 @@ cudaError_t dispatch_warp(int d, const WarpJob& job, cudaStream_t s) {
   }
 }
 
+cudaError_t warp_job_f32_hi(int d, const WarpJob& job, cudaStream_t s);
+cudaError_t warp_job_f64_hi(int d, const WarpJob& job, cudaStream_t s);
 cudaError_t warp_job_f64(int d, const WarpJob& job, cudaStream_t s);
 cudaError_t warp_job_f32(int d, const WarpJob& job, cudaStream_t s);
 

@@ -172,23 +172,25 @@ def test_invalid_method_is_rejected(L, H):
         L.lmep_set_expm_method(H, "taylor")
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_graph_replay_matches_eager_steps(L, precision):
-    """FrozenSet: K steps replayed from one captured CUDA graph equal K eager library calls bit for
-    bit (three instances of different n and dt, one with Pade rows)."""
+def test_graph_replay_matches_eager_steps(L, precision, fused):
+    """FrozenSet: K steps replayed from captured CUDA graphs equal K eager steps bit for bit (three
+    instances of different n and dt, one with Pade rows), as one launch per step (fused) and as one
+    library call per instance."""
     from paper_2603_15964_gb300.frozen import FrozenInstance, FrozenSet
     probs = [wl.burgers(N=4099, n=7, cfl=2.0, nu=1e-6), wl.burgers(N=2048, n=13, cfl=4.0, nu=4e-4),
              wl.burgers(N=3001, n=9, cfl=1.0, nu=1e-6)]
     insts = [FrozenInstance(grid_of(p), op_of(p), p.dt) for p in probs]
     u0 = [wl.burgers_ic(p.N, s) for s, p in enumerate(probs)]
     K = 5
-    eager = FrozenSet(insts, precision=precision)
+    eager = FrozenSet(insts, precision=precision, fused=fused)
     eager.load(u0)
     eager.step(K)
-    graph = FrozenSet(insts, precision=precision)
+    graph = FrozenSet(insts, precision=precision, fused=fused)
     graph.load(u0)
-    graph.capture()               # one eager warm-up step
-    graph.replay(K - 1)
+    graph.capture()               # eager warm-up: two steps (fused, one per direction) or one
+    graph.replay(K - (2 if fused else 1))
     torch.cuda.synchronize()
     for a, b in zip(eager.states, graph.states):
         assert torch.equal(a, b)
