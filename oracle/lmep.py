@@ -20,9 +20,21 @@
   same departure point.  With k the rounded Courant number the matrix norm
   drops by 5-20x and the FP64 error of the Pade evaluation from ~5e-12 to
   ~5e-15 at n = 13, CFL 4.  ``recentre=False`` gives the plain form.
+* ETDRK4 (Sec. 3, the Cox-Matthews stages a, b, c of Kassam & Trefethen):
+      a  = e^{L dt/2} u + (dt/2) phi_1(L dt/2) N(u)
+      b  = e^{L dt/2} u + (dt/2) phi_1(L dt/2) N(a)
+      c  = e^{L dt/2} a + (dt/2) phi_1(L dt/2) (2 N(b) - N(u))
+      u+ = e^{L dt} u + dt [alpha N(u) + beta (N(a) + N(b)) + gamma N(c)]
+  with alpha = phi_1 - 3 phi_2 + 4 phi_3, beta = 2 phi_2 - 4 phi_3,
+  gamma = 4 phi_3 - phi_2 at L dt.  The rows of e^{L dt} and dt^k phi_k
+  (k <= 3) come from the augmented local matrix with p = 3 at dt, those of
+  e^{L dt/2} and (dt/2) phi_1(L dt/2) from the one with p = 1 at dt/2
+  (Sec. 3.1); the rows of dt alpha, dt beta, dt gamma are the combinations of
+  the harvested rows.  Every stage keeps the Dirichlet wall values.
 * Nonlinear terms: Allen-Cahn N(u) = u - u^3 (Sec. 4.3.3, L = eps2 d^2/dx^2);
   KdV N(u) = -6 u u_x with u_x from row r_i of D^(1) on the same stencil
-  (L = -d^3/dx^3); frozen-velocity Burgers has N = 0 and the operator
+  (L = -d^3/dx^3); Burgers with ETD N(u) = -u u_x the same way (Sec. 4.3.1,
+  L = nu d^2/dx^2); frozen-velocity Burgers has N = 0 and the operator
   -u_i D^(1) + nu D^(2) rebuilt at every point and step.
 Test infrastructure only.
 """
@@ -86,14 +98,15 @@ def nonlinear(p: Problem, u: np.ndarray, D=None) -> np.ndarray:
         return np.zeros_like(u)
     if p.nonlin == "allen_cahn":
         return u - u ** 3
-    if p.nonlin == "kdv":
+    if p.nonlin in ("kdv", "burgers"):
         if D is None:
             D = unit_D(p.n)
+        coef = -6.0 if p.nonlin == "kdv" else -1.0
         out = np.zeros_like(u)
         for i in range(p.N):
             idx, r = grid.stencil(p, i)
             ux = (D[1][r] @ u[idx]) / p.h
-            out[i] = -6.0 * u[i] * ux
+            out[i] = coef * u[i] * ux
         return out
     raise ValueError(p.nonlin)
 
@@ -113,8 +126,42 @@ def _walls(p: Problem, v: np.ndarray) -> np.ndarray:
     return v
 
 
-def step(p: Problem, W: np.ndarray, u: np.ndarray, D=None) -> np.ndarray:
-    """One step with stored constant-coefficient weights W[n][1+n_phi][n]."""
+def half_step_weights(p: Problem) -> np.ndarray:
+    """ETDRK4: rows of e^{L dt/2} and (dt/2) phi_1(L dt/2), [n][2][n] (augmented, p = 1, at dt/2)."""
+    return constant_weights(p.with_(dt=p.dt / 2.0, scheme="etd1"))
+
+
+def etdrk4_coefficient_rows(p: Problem, W: np.ndarray):
+    """Rows of dt alpha, dt beta, dt gamma from the harvested rows w_k of dt^k phi_k (k = 1..3)."""
+    w1, w2, w3 = W[:, 1], W[:, 2] / p.dt, W[:, 3] / p.dt ** 2        # rows of dt phi_1, dt phi_2, dt phi_3
+    return w1 - 3.0 * w2 + 4.0 * w3, 2.0 * w2 - 4.0 * w3, 4.0 * w3 - w2
+
+
+def _banded_rows(p: Problem, R: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """(sum_j R[r_i, j] v[idx_i[j]])_i over the updated points; zero elsewhere."""
+    out = np.zeros_like(v)
+    for i in grid.updated_points(p):
+        idx, r = grid.stencil(p, i)
+        out[i] = R[r] @ v[idx]
+    return out
+
+
+def step(p: Problem, W: np.ndarray, u: np.ndarray, D=None, Wh: np.ndarray | None = None) -> np.ndarray:
+    """One step with stored constant-coefficient weights W[n][1+n_phi][n] (and, for ETDRK4, the
+    half-step rows Wh[n][2][n])."""
+    if p.scheme == "etdrk4":
+        if Wh is None:
+            Wh = half_step_weights(p)
+        Nu = nonlinear(p, u, D)
+        a = _walls(p, _banded(p, Wh, 0, u) + _banded(p, Wh, 1, Nu))
+        Na = nonlinear(p, a, D)
+        b = _walls(p, _banded(p, Wh, 0, u) + _banded(p, Wh, 1, Na))
+        Nb = nonlinear(p, b, D)
+        c = _walls(p, _banded(p, Wh, 0, a) + _banded(p, Wh, 1, 2.0 * Nb - Nu))
+        Nc = nonlinear(p, c, D)
+        alpha, beta, gamma = etdrk4_coefficient_rows(p, W)
+        return _walls(p, _banded(p, W, 0, u) + _banded_rows(p, alpha, Nu) + _banded_rows(p, beta, Na + Nb)
+                      + _banded_rows(p, gamma, Nc))
     if p.scheme == "linear":
         return _walls(p, _banded(p, W, 0, u))
     Nu = nonlinear(p, u, D)
@@ -149,8 +196,9 @@ def run(p: Problem, u0: np.ndarray, steps: int | None = None) -> np.ndarray:
             u = frozen_step(p, u, D)
         return u
     W = constant_weights(p)
+    Wh = half_step_weights(p) if p.scheme == "etdrk4" else None
     for _ in range(steps):
-        u = step(p, W, u, D)
+        u = step(p, W, u, D, Wh)
     return u
 
 

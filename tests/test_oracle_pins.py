@@ -446,3 +446,116 @@ def test_stability_precheck_closed_form():
         G = lmep.amplification(w, 2, np.array([np.pi]))[0]
         assert abs(G - (1 - 16 * mu / 3 + 8 * mu * mu)) < 1e-13
     assert abs(1 - 16 * (2 / 3) / 3 + 8 * (2 / 3) ** 2 - 1.0) < 1e-15
+
+
+# ------------------------------------------------------------ ETDRK4 (Sec. 3)
+def _phi(k, z):
+    """phi_k(z) by the paper's recursion phi_0 = e^z, phi_{j+1} = (phi_j - 1/j!) / z (z away from 0)."""
+    v = math.exp(z)
+    for j in range(k):
+        v = (v - 1.0 / math.factorial(j)) / z
+    return v
+
+
+def test_etdrk4_is_classical_rk4_without_linear_part_and_order4_with_it():
+    """L = 0: the stages a, b, c and the alpha, beta, gamma combination reduce to the classical
+    fourth-order Runge-Kutta method (phi_k(0) = 1/k!); with L = c0 it keeps order 4.  Both against
+    the closed-form solution of u' = (1 + c0) u - u^3 (a Bernoulli equation)."""
+    u0 = np.array([0.1, -0.5, 0.9, 0.3, 0.05])
+    T = 1.0
+    for c0 in (0.0, -2.0):
+        a = 1.0 + c0
+        exact_sol = u0 * math.exp(a * T) / np.sqrt(1 + u0 * u0 * (math.exp(2 * a * T) - 1) / a)
+        errs = []
+        for m in (10, 20, 40, 80):
+            p = wl.Problem("rx", 5, 0.0, 1.0, wl.PERIODIC, 3, T / m, c0=c0, scheme="etdrk4", nonlin="allen_cahn")
+            errs.append(np.max(np.abs(lmep.run(p, u0, m) - exact_sol)))
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+        assert all(abs(r - 4.0) < 0.15 for r in rates), (c0, rates)
+    # L = 0, one step: exactly the classical RK4 weights 1/6, 1/3, 1/3, 1/6
+    dt = 0.3
+    f = lambda v: v - v ** 3
+    k1 = f(u0)
+    k2 = f(u0 + dt / 2 * k1)
+    k3 = f(u0 + dt / 2 * k2)
+    k4 = f(u0 + dt * k3)
+    rk4 = u0 + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    p = wl.Problem("rx", 5, 0.0, 1.0, wl.PERIODIC, 3, dt, scheme="etdrk4", nonlin="allen_cahn")
+    assert np.max(np.abs(lmep.run(p, u0, 1) - rk4)) < 1e-15
+
+
+def test_etdrk4_rows_closed_forms():
+    """Pure reaction L = c0: the harvested rows are scalars, dt^k phi_k(dt c0) (k <= 3) at dt and
+    e^{c0 dt/2}, (dt/2) phi_1(c0 dt/2) at dt/2; the rows of dt alpha, dt beta, dt gamma are
+    dt (phi_1 - 3 phi_2 + 4 phi_3), dt (2 phi_2 - 4 phi_3), dt (4 phi_3 - phi_2) (Sec. 3)."""
+    c0, dt = -3.0, 0.3
+    z = c0 * dt
+    p = wl.Problem("lin", 5, 0.0, 1.0, wl.PERIODIC, 3, dt, c0=c0, scheme="etdrk4", nonlin="allen_cahn")
+    W = lmep.constant_weights(p)
+    for k in range(4):
+        assert abs(W[1, k, 1] - dt ** k * _phi(k, z)) < 1e-15 * max(1.0, dt ** k), k
+        assert abs(W[1, k, 0]) < 1e-15 and abs(W[1, k, 2]) < 1e-15
+    Wh = lmep.half_step_weights(p)
+    assert abs(Wh[1, 0, 1] - math.exp(z / 2)) < 1e-15
+    assert abs(Wh[1, 1, 1] - dt / 2 * _phi(1, z / 2)) < 1e-15
+    al, be, ga = lmep.etdrk4_coefficient_rows(p, W)
+    p1, p2, p3 = _phi(1, z), _phi(2, z), _phi(3, z)
+    assert abs(al[1, 1] - dt * (p1 - 3 * p2 + 4 * p3)) < 1e-14
+    assert abs(be[1, 1] - dt * (2 * p2 - 4 * p3)) < 1e-14
+    assert abs(ga[1, 1] - dt * (4 * p3 - p2)) < 1e-14
+    # Kassam & Trefethen's explicit forms of the same three functions
+    assert abs(al[1, 1] - dt * (-4 - z + math.exp(z) * (4 - 3 * z + z * z)) / z ** 3) < 1e-13
+    assert abs(be[1, 1] - dt * 2 * (2 + z + math.exp(z) * (z - 2)) / z ** 3) < 1e-13
+    assert abs(ga[1, 1] - dt * (-4 - 3 * z - z * z + math.exp(z) * (4 - z)) / z ** 3) < 1e-13
+
+
+def test_etdrk4_weight_sums_are_rk4_weights():
+    """c0 = 0: every row of dt^k phi_k(X) sums to dt^k / k! (constants are annihilated), so the rows
+    of dt alpha, dt beta, dt gamma sum to dt/6, dt/3, dt/6, the classical weights."""
+    p = wl.Problem("r", 40, 0.0, 1.0, wl.DIRICHLET, 11, 0.0, c1=-0.8, c2=0.02, c3=-0.001, scheme="etdrk4",
+                   nonlin="allen_cahn")
+    p = p.with_(dt=0.9 * p.h)
+    W = lmep.constant_weights(p)
+    al, be, ga = lmep.etdrk4_coefficient_rows(p, W)
+    for r in range(p.n):       # to the rounding of the sums: 1e-13 of the rows' absolute sums
+        for row, want in ((W[r, 3], p.dt ** 3 / 6), (al[r], p.dt / 6), (be[r], p.dt / 3), (ga[r], p.dt / 6)):
+            assert abs(np.sum(row) - want) < 1e-13 * np.sum(np.abs(row)), r
+
+
+def test_etdrk4_phi3_rows_match_taylor_and_block_form():
+    """Row r of dt^3 phi_3(X) = dt^3 sum_j X^j/(j+3)! (finite: X nilpotent) and equals the paper's
+    s n x s n block form with s = 4 (Sec. 3.1)."""
+    n, c1, c2, c3, dt = 5, 1.3, 0.4, -0.05, 0.37
+    Xf = exact.local_matrix(n, dt, 1.0, c1, c2, c3)
+    X = exact.to_float(Xf)
+    p = wl.Problem("phi", 30, 0.0, 29.0, wl.DIRICHLET, n, dt, c1=c1, c2=c2, c3=c3, scheme="etdrk4")
+    acc = [[Fraction(0)] * n for _ in range(n)]
+    term = [[Fraction(int(i == j)) for j in range(n)] for i in range(n)]
+    for j in range(n):
+        f = Fraction(1, math.factorial(j + 3))
+        acc = [[acc[a][b] + f * term[a][b] for b in range(n)] for a in range(n)]
+        term = exact.matmul(term, Xf)
+    phi3 = exact.to_float(acc) * dt ** 3
+    E = ox.expm(operator.augmented_block(X, dt, 4))
+    for r in range(n):
+        got = lmep.harvest(p, X, r)
+        assert np.max(np.abs(got[3] - phi3[r])) <= 1e-13 * max(dt ** 3, np.max(np.abs(phi3[r])))
+        for k in range(4):
+            want = E[r, k * n:(k + 1) * n]
+            assert np.max(np.abs(got[k] - want)) < 1e-13 * max(1.0, np.max(np.abs(want)))
+
+
+def test_etdrk4_without_nonlinearity_is_the_exponential_step():
+    p = wl.allen_cahn(64, bc=wl.NEUMANN, n=9, scheme="etdrk4", steps=3, mu=0.8).with_(nonlin="none")
+    u0 = np.cos(np.pi * p.nodes()) + 0.2 * np.sin(5 * p.nodes())
+    lin = p.with_(scheme="linear")
+    # the same exponential rows (augmented harvest vs the re-centred plain one, both FP64 Pade)
+    assert np.max(np.abs(lmep.run(p, u0) - lmep.run(lin, u0))) < 1e-12
+
+
+def test_burgers_etd_nonlinearity_is_minus_u_ux():
+    """N(u) = -u u_x with u_x from row r of D^(1): exact for a quadratic u = x^2 (n >= 3)."""
+    p = wl.burgers_etd(N=64, n=7).with_(bc=wl.DIRICHLET, a=0.0, b=1.0)
+    x = p.nodes()
+    got = lmep.nonlinear(p, x ** 2)
+    assert np.max(np.abs(got - (-(x ** 2) * 2 * x))) < 1e-12

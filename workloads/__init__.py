@@ -20,8 +20,8 @@ import numpy as np
 
 PERIODIC, DIRICHLET, NEUMANN = "periodic", "dirichlet", "neumann"
 BC_CODE = {PERIODIC: 0, DIRICHLET: 1, NEUMANN: 2}
-SCHEME_CODE = {"linear": 0, "etd1": 1, "etdrk2": 2}
-NONLIN_CODE = {"none": 0, "allen_cahn": 1, "kdv": 2}
+SCHEME_CODE = {"linear": 0, "etd1": 1, "etdrk2": 2, "etdrk4": 3}
+NONLIN_CODE = {"none": 0, "allen_cahn": 1, "kdv": 2, "burgers": 3}
 
 
 @dataclass(frozen=True)
@@ -60,7 +60,7 @@ class Problem:
 
     @property
     def n_phi(self) -> int:
-        return {"linear": 0, "etd1": 1, "etdrk2": 2}[self.scheme]
+        return {"linear": 0, "etd1": 1, "etdrk2": 2, "etdrk4": 3}[self.scheme]
 
     def nodes(self) -> np.ndarray:
         return self.a + self.h * np.arange(self.N, dtype=np.float64)
@@ -175,6 +175,20 @@ def kdv_ic(p: Problem, seed: int = 0) -> np.ndarray:
     for k, x0 in zip(kap, xs * scale):
         u += 2.0 * k * k / np.cosh(k * (x - x0)) ** 2
     return u
+
+
+# ---------------------------------------------------------------- Burgers with ETD (Sec. 4.3.1)
+def burgers_etd(N: int = 128, n: int = 13, nu: float = 0.03, dt: float = 1e-2, scheme: str = "etdrk4",
+                steps: int = 100) -> Problem:
+    """Viscous Burgers u_t + u u_x = nu u_xx, periodic on [-pi, pi): L = nu d^2/dx^2 (exponentiated),
+    N(u) = -u u_x (the paper's Sec. 4.3.1 benchmark, nu = 0.03)."""
+    return Problem("burgers_etd", N, -math.pi, math.pi, PERIODIC, n, dt, c2=nu, scheme=scheme,
+                   nonlin="burgers", steps=steps)
+
+
+def burgers_etd_ic(p: Problem) -> np.ndarray:
+    """exp(-10 sin^2(x / 2)) (Sec. 4.3.1)."""
+    return np.exp(-10.0 * np.sin(p.nodes() / 2.0) ** 2)
 
 
 # ---------------------------------------------------------------- config 5
