@@ -27,7 +27,7 @@ constexpr int MAXW = DMAX * 3 * DMAX;  // n * (1 + n_phi) * n, n <= 15, n_phi <=
 // even when the last tile is shorter than a stencil.
 int apply_halo(int n, int scheme, int nonlin, int bc) {
   const int hs = (n - 1) / 2;
-  const int hN = nonlin == 2 ? hs : 0;
+  const int hN = nonlin >= 2 ? hs : 0;
   int H = scheme == 0 ? hs : (scheme == 1 ? hs + hN : 2 * hs + 2 * hN);
   if (bc == BC_DIRICHLET) H += hs;
   return H;
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(512) k_apply(ApplyParams a, const ST* __restri
   ST* sW = reinterpret_cast<ST*>(smem);
   ST* sd1 = sW + MAXW;
   const int n = a.n, hs = (n - 1) >> 1;
-  constexpr bool KDV = NONLIN == 2;
+  constexpr bool KDV = NONLIN >= 2;                 // a derivative nonlinearity: KdV or Burgers
+  const ST ncoef = ST(NONLIN == 2 ? -6 : -1);         // N = ncoef u u_x
   const int hN = KDV ? hs : 0;
   const int H = a.halo;
   const int Lmax = a.tile + 2 * H;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(512) k_apply(ApplyParams a, const ST* __restri
       // Dirichlet needs every row class; periodic and Neumann only the centre row.
       const ST* Wb = W + b * a.w_stride;
       const int nq = SCHEME + 1;
-      const int r0 = dir ? 0 : hs, r1 = dir ? n : hs + 1;
+      const int r0 = dir ? 0 : hs + a.shift, r1 = dir ? n : hs + a.shift + 1;
       for (int e = threadIdx.x; e < (r1 - r0) * nq * n; e += blockDim.x) {
         const int r = r0 + e / (nq * n), rem = e % (nq * n);
         sW[(r * 3 + rem / n) * DMAX + rem % n] = Wb[(r * wq + rem / n) * n + rem % n];
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(512) k_apply(ApplyParams a, const ST* __restri
         if (KDV) {
           ST ux = ST(0);
           for (int j = 0; j < n; ++j) ux = fma(sd1[j], su[q - hs + j], ux);
-          f = ST(-6) * x * ux * inv_h;
+          f = ncoef * x * ux * inv_h;
         } else {
           f = x - x * x * x;
         }
@@ -126,13 +127,13 @@ __global__ void __launch_bounds__(512) k_apply(ApplyParams a, const ST* __restri
     auto window = [&](int q, int& ls, int& r) {
       if (dir) {
         const int64_t i = base + q;
-        int64_t st = i - hs;
+        int64_t st = i - hs - a.shift;
         st = st < 0 ? 0 : (st > N - n ? N - n : st);
         ls = int(st - base);
         r = int(i - st);
       } else {
-        ls = q - hs;
-        r = hs;
+        ls = q - hs - a.shift;
+        r = hs + a.shift;
       }
     };
     if (SCHEME == 0) {
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(512) k_apply(ApplyParams a, const ST* __restri
       if (KDV) {
         ST ux = ST(0);
         for (int j = 0; j < n; ++j) ux = fma(sd1[j], sa[q - hs + j], ux);
-        f = ST(-6) * x * ux * inv_h;
+        f = ncoef * x * ux * inv_h;
       } else {
         f = x - x * x * x;
       }
@@ -263,8 +264,11 @@ cudaError_t launch_pair_tables(const void* W, int64_t w_stride, int wq, int n, i
 template <typename ST>
 static const void* pick(int scheme, int nonlin) {
   if (scheme == 0) return (const void*)k_apply<ST, 0, 0>;
-  if (scheme == 1) return nonlin == 2 ? (const void*)k_apply<ST, 1, 2> : (const void*)k_apply<ST, 1, 1>;
-  return nonlin == 2 ? (const void*)k_apply<ST, 2, 2> : (const void*)k_apply<ST, 2, 1>;
+  if (scheme == 1)
+    return nonlin == 3 ? (const void*)k_apply<ST, 1, 3>
+                       : (nonlin == 2 ? (const void*)k_apply<ST, 1, 2> : (const void*)k_apply<ST, 1, 1>);
+  return nonlin == 3 ? (const void*)k_apply<ST, 2, 3>
+                     : (nonlin == 2 ? (const void*)k_apply<ST, 2, 2> : (const void*)k_apply<ST, 2, 1>);
 }
 
 // The fast kernels hard-wire the Allen-Cahn nonlinearity for ETD schemes; with
