@@ -6,25 +6,35 @@ Workload (one "step"): one time step of frozen-velocity viscous Burgers on
 (stencil width n, Courant number) pairs n in {7, 9, 13} x CFL in {1, 2, 4}
 (dt = CFL h / max|u0|), nu = 1e-6 (the stable variant of the stated nu = 1e-3),
 departure-centred windows.  Every point rebuilds and exponentiates its local
-operator at every step (a1-a6 fused in one launch per instance).
+operator at every step; the nine instances advance together as one
+frozen-velocity set: one persistent launch per step (a1-a6 fused) plus the
+launch that finishes the points the first one rejects.
 
-value      point-updates/s of the FP32 form, inputs resident: each row of
-           exp(X), X = a D1 + E, as l(r + a)^T exp(E) (Lagrange weights times
-           the exponential of the point-independent part, computed once per
-           instance in FP64) where its bound allows, else from the finite
+value      point-updates/s of the FP32 form, inputs resident, the K timed
+           steps plus 1/1000 of the run's setup (every instance's exp(E), one
+           launch) per step: each row of exp(X), X = a D1 + E, as
+           l(r + a)^T exp(E) (Lagrange weights times the exponential of the
+           point-independent part) where its bound allows, else the finite
            Taylor series of the nilpotent local matrix, else Pade scaling and
            squaring; FP32 apply.
 fp64       the same for the plain FP64 path.
 pade_route the FP32 form with Pade scaling and squaring for every row.
+unfused    the FP32 form as nine separate library calls per step.
 e2e        the FP32 form through the public API with host buffers: every step
-           copies the states in from pinned host memory and the result back.
-roofline   the dominant kernel (the n = 13 launches), ALU-bound: achieved
-           FP32-equivalent FLOP/s of the algorithm's own work per launch.
-cpu_baseline  the FP64 oracle on the host cores (spawn pool) on a bounded
-           sample of points of the same step; its outputs also give the
-           stated error of both GPU paths.
+           copies the packed state in from pinned host memory and back.
+roofline   the step's two launches, ALU-bound: achieved FP32-equivalent
+           FLOP/s of the algorithm's own work per step.
+cpu_baseline  the C build of the FP64 oracle (OpenMP over points, all host
+           cores) on every point of the same step; its outputs also give the
+           stated error of the GPU legs.
+configs    every other configuration, each with its own timer: config 1
+           (advection-diffusion, us per run), config 3 (the 4096-instance
+           Allen-Cahn batch, HBM roofline), config 4 (KdV, FP64 and FP32,
+           invariant drift), config 5 (adjoint, reduced batch), the apply sweep,
+           ETDRK4 on the paper's Burgers benchmark, a non-uniform grid, and the
+           one-sided high-CFL advection study.
 
---impl reference runs that oracle alone (each step a bounded sample).
+--impl reference runs the oracle alone (each step a bounded sample).
 Multi-GPU (torchrun): every rank advances its own independent set of nine
 instances (weak scaling, no collective on the data path).
 """
@@ -909,6 +919,323 @@ def apply_sweep_main(args, rank, world, local_rank, cores):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ the other configurations (one run)
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed_ms(fn, reps: int = 1) -> float:
+    """Device time of reps calls of fn() (CUDA events on the current stream), ms per call."""
+    import torch
+    a, b = _events()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def cfg1_advection_diffusion(L, h):
+    """Config 1: periodic u_t + u_x = 0.01 u_xx on [0, 2 pi), N = 256, n = 5, CFL 0.8, 100 steps, FP64:
+    the whole run (weights harvested once, then 100 steps) timed, error against the closed-form solution
+    (the sine decays as e^{-nu t}, the Gaussian spreads and is summed over periodic images)."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    p = wl.advection_diffusion(N=256, n=5, steps=100)
+    g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n)
+    op = L.Operator(c1=p.c1, c2=p.c2)
+    u0 = torch.tensor(wl.advection_diffusion_ic(p), device="cuda")
+    W = torch.empty(p.n, 1, p.n, dtype=torch.float64, device="cuda")
+    u = u0.clone()
+    work = torch.empty_like(u)
+
+    def run():
+        u.copy_(u0)
+        L.lmep_harvest_weights(h, g, op, p.dt, 0, None, W, "fp64")
+        L.lmep_step(h, g, op, "linear", "none", p.dt, W, u, work, p.steps, "fp64")
+
+    run()
+    ms = min(_timed_ms(run) for _ in range(5))
+    L.lmep_sync_status(h)
+    t = p.steps * p.dt
+    x = p.nodes()
+    nu, c = p.c2, -p.c1
+    exact = np.exp(-nu * t) * np.sin(x - c * t)
+    s2 = 1 + 80 * nu * t
+    for k in range(-2, 3):
+        z = x - np.pi - c * t - 2 * np.pi * k
+        exact += np.exp(-20 * z ** 2 / s2) / np.sqrt(s2)
+    err = float(np.max(np.abs(u.cpu().numpy() - exact)))
+    return {"workload": "periodic advection-diffusion, N = 256, n = 5, CFL 0.8, nu = 0.01, 100 steps, FP64",
+            "us_per_run": 1e3 * ms, "point_updates_per_s": p.N * p.steps / (ms * 1e-3),
+            "error_vs_exact_linf": err, "roofline": "latency-bound (a 2 KB state); none reported",
+            "note": "run = one harvest launch + 100 step launches + copy back, CUDA events, best of 5"}
+
+
+def cfg3_allen_cahn(L, steps: int = 50):
+    """Config 3: the 4096-instance Allen-Cahn ETDRK2 batch in one persistent launch per step (graph
+    replay), HBM roofline, error of one step against the oracle on the 8 smallest instances."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from oracle import lmep as olmep
+    from paper_2603_15964_gb300.batch import BatchedProblem, LaunchShape, autotune, pack
+    batch = wl.allen_cahn_batch(B=4096, seed=0, steps=steps)
+    B = len(batch.Ns)
+    hs = [batch.problem(b).h for b in range(B)]
+    op = L.Operator(c2=batch.eps2)
+    cands = [LaunchShape(t, bl, 0) for t in (512, 1024, 2048) for bl in (64, 128, 256)]
+    shape, _ = autotune(batch.Ns, hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",
+                        candidates=cands, use_cache=False)
+    prob = BatchedProblem(list(batch.Ns), hs, batch.bcs, batch.n, "etdrk2", "allen_cahn", batch.dt, op, "mixed",
+                          shape)
+    u0s = [wl.allen_cahn_ic(int(batch.Ns[b]), b) for b in range(B)]
+    u = pack(u0s, torch.float32)
+    work = torch.empty_like(u)
+    first = torch.empty_like(u)
+    L.lmep_step_batched_once(prob.handle, prob.workspace, u, first)
+    prob.capture(u, work)
+    prob.replay(6)
+    ms = _timed_ms(lambda: prob.replay(steps)) / steps
+    L.lmep_sync_status(prob.handle)
+    peak, src = measured_hbm_peak()
+    gbs = 8.0 * prob.points / (ms * 1e-3) / 1e9
+    got = first.cpu().numpy()
+    worst = 0.0
+    for b in np.argsort(batch.Ns)[:8]:
+        o = prob.offsets[b]
+        want = olmep.run(batch.problem(int(b)), u0s[b].astype(np.float32).astype(np.float64), 1)
+        worst = max(worst, float(np.max(np.abs(got[o:o + int(batch.Ns[b])] - want)) / np.max(np.abs(want))))
+    return {"workload": f"{B} Allen-Cahn instances (N log-uniform in [1024, 65536], {prob.points} points), "
+                        "n = 9, ETDRK2, FP32, one persistent launch per step from a CUDA graph",
+            "point_updates_per_s": prob.points / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "peak_source": src, "algorithmic_bytes_per_point_update": 8},
+            "launch_shape": shape.__dict__, "error_vs_oracle_rel_linf": worst,
+            "error_sample": "one step of the 8 smallest instances (FP32 initial states)"}
+
+
+def cfg4_kdv(L, h, steps: int = 200):
+    """Config 4: KdV u_t + 6 u u_x + u_xxx = 0, periodic, N = 2^20, n = 11, ETDRK2, dt = 0.05 h^3, FP64
+    and FP32: step rate and the drift of the invariants I1 = sum u h and I2 = sum u^2 h over the run."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    p = wl.kdv(N=1 << 20, n=11, steps=steps)
+    g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n)
+    op = L.Operator(c3=p.c3)
+    u0 = wl.kdv_ic(p, 0)
+    out = {"workload": f"KdV, N = 2^20 on [-50, 50), n = 11, ETDRK2, dt = 0.05 h^3, {steps} steps"}
+    for prec in ("fp64", "mixed"):
+        dt_ = L.state_dtype(prec)
+        W = torch.empty(p.n, 3, p.n, dtype=dt_, device="cuda")
+        L.lmep_harvest_weights(h, g, op, p.dt, 2, None, W, prec)
+        u = torch.tensor(u0, dtype=dt_, device="cuda")
+        work = torch.empty_like(u)
+        L.lmep_step(h, g, op, "etdrk2", "kdv", p.dt, W, u, work, 2, prec)
+        u.copy_(torch.tensor(u0, dtype=dt_))
+        ms = _timed_ms(lambda: L.lmep_step(h, g, op, "etdrk2", "kdv", p.dt, W, u, work, steps, prec)) / steps
+        L.lmep_sync_status(h)
+        v = u.double().cpu().numpy()
+        i1 = abs(np.sum(v) - np.sum(u0)) / abs(np.sum(u0))
+        i2 = abs(np.sum(v ** 2) - np.sum(u0 ** 2)) / np.sum(u0 ** 2)
+        out[prec] = {"point_updates_per_s": p.N / (ms * 1e-3), "ms_per_step": ms,
+                     "hbm_GB_s": 2.0 * (8 if prec == "fp64" else 4) * p.N / (ms * 1e-3) / 1e9,
+                     "I1_rel_drift": float(i1), "I2_rel_drift": float(i2)}
+    out["note"] = "the state (8 / 4 MB) stays in L2; HBM figures are nominal bytes over time"
+    return out
+
+
+def cfg5_adjoint(L, B: int = 8, K: int = 4):
+    """Config 5 shape (N = 262144 per instance, frozen Burgers, n = 9, CFL 2): forward and reverse of K
+    steps of B instances through torch.autograd (checkpoint every 2), gradient point-steps/s."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2603_15964_gb300.autograd import FrozenVelocitySolver
+    p = adj_problem(K)
+    x0 = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, q) for q in range(B)]).astype(np.float32), device="cuda")
+    tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + q) for q in range(B)]), dtype=torch.float32,
+                       device="cuda")
+    solver = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="mixed", checkpoint_every=2)
+
+    def once():
+        x = x0.clone().requires_grad_(True)
+        nu = torch.tensor(p.c2, dtype=torch.float64, requires_grad=True)
+        J = 0.5 * p.h * ((solver(x, nu) - tgt) ** 2).sum()
+        J.backward()
+        return x.grad, nu.grad
+
+    once()
+    ms = min(_timed_ms(once) for _ in range(3))
+    L.lmep_sync_status(solver.handle)
+    return {"workload": f"adjoint of frozen Burgers, {B} x N = {ADJ_N}, n = 9, CFL 2, nu = 1e-6, {K} steps "
+                        "forward + reverse (checkpoint every 2), FP32 forward, FP64 derivatives",
+            "gradient_point_steps_per_s": ADJ_N * B * K / (ms * 1e-3), "ms": ms}
+
+
+def cfg_apply_sweep(L, h, log2n: int = 26, K: int = 20):
+    """The stand-alone stored-weight apply on one periodic instance of 2^26 points (state larger than L2):
+    HBM throughput of the linear apply (n = 5, 9, 15) and of Allen-Cahn ETDRK2 (n = 9), FP32 and FP64."""
+    import numpy as np
+    import torch
+    N = 1 << log2n
+    peak, src = measured_hbm_peak()
+    rows = []
+    for prec in ("mixed", "fp64"):
+        es = 4 if prec == "mixed" else 8
+        dt_ = L.state_dtype(prec)
+        x = torch.linspace(-1.0, 1.0, N + 1, dtype=torch.float64, device="cuda")[:-1]
+        u = (0.5 * torch.sin(np.pi * x) + 0.05 * torch.sin(40 * np.pi * x)).to(dt_)
+        del x
+        w = torch.empty_like(u)
+        hh = 2.0 / N
+        for n, scheme, nonlin in ((5, "linear", "none"), (9, "linear", "none"), (15, "linear", "none"),
+                                  (9, "etdrk2", "allen_cahn")):
+            if scheme == "linear":
+                op, dtv = L.Operator(c1=-1.0, c2=1e-4 * hh), 0.5 * hh
+            else:
+                op, dtv = L.Operator(c2=1e-4), 0.5 * hh * hh / 1e-4
+            g = L.Grid(N=N, h=hh, bc="periodic", n=n)
+            W = torch.empty(n, L.scheme_rows(scheme), n, dtype=dt_, device="cuda")
+            L.lmep_harvest_scheme_weights(h, g, op, dtv, scheme, W, prec)
+            L.lmep_step(h, g, op, scheme, nonlin, dtv, W, u, w, 4, prec)
+            ms = _timed_ms(lambda: L.lmep_step(h, g, op, scheme, nonlin, dtv, W, u, w, K, prec)) / K
+            gbs = 2.0 * es * N / (ms * 1e-3) / 1e9
+            rows.append({"precision": prec, "n": n, "scheme": scheme, "ms_per_step": ms, "GB_s": gbs,
+                         "frac": gbs / peak})
+        del u, w
+        torch.cuda.empty_cache()
+    L.lmep_sync_status(h)
+    return {"workload": f"one periodic instance of 2^{log2n} points, stored weights, {K} steps per case",
+            "peak": peak, "peak_source": src, "unit": "GB/s (read u + write u+ per point-update)", "rows": rows}
+
+
+def cfg_etdrk4(L, h, K: int = 20):
+    """ETDRK4 (the paper's Sec. 3 scheme) on its viscous Burgers benchmark (Sec. 4.3.1: nu = 0.03, periodic
+    [-pi, pi), N(u) = -u u_x) at N = 2^22, n = 13: step rate and HBM throughput, FP32 and FP64."""
+    import torch
+    import workloads as wl
+    p = wl.burgers_etd(N=1 << 22, n=13, nu=0.03, dt=0.0, steps=K)
+    p = p.with_(dt=0.5 * p.h * p.h / p.c2)          # mu = nu dt / h^2 = 0.5 (stable for n = 13)
+    g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n)
+    op = L.Operator(c2=p.c2)
+    peak, src = measured_hbm_peak()
+    out = {"workload": f"viscous Burgers (nu = 0.03) with ETDRK4, periodic, N = 2^22, n = 13, nu dt / h^2 = 0.5, "
+                       f"{K} steps",
+           "peak": peak, "peak_source": src}
+    u0 = wl.burgers_etd_ic(p)
+    for prec in ("mixed", "fp64"):
+        dt_ = L.state_dtype(prec)
+        es = 4 if prec == "mixed" else 8
+        W = torch.empty(p.n, 6, p.n, dtype=dt_, device="cuda")
+        L.lmep_harvest_scheme_weights(h, g, op, p.dt, "etdrk4", W, prec)
+        u = torch.tensor(u0, dtype=dt_, device="cuda")
+        work = torch.empty_like(u)
+        L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, work, 2, prec)
+        ms = _timed_ms(lambda: L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, work, K, prec)) / K
+        gbs = 2.0 * es * p.N / (ms * 1e-3) / 1e9
+        out[prec] = {"point_updates_per_s": p.N / (ms * 1e-3), "ms_per_step": ms, "GB_s": gbs, "frac": gbs / peak}
+    L.lmep_sync_status(h)
+    return out
+
+
+def cfg_nonuniform(L, h, log2n: int = 21, K: int = 20):
+    """Non-uniform grid (Sec. 4.3.3): a stretched grid of 2^21 nodes on [-1, 1] with Dirichlet walls, every
+    node's rows harvested once (one warp per node), then ETD1 Allen-Cahn steps that read each node's
+    stored rows: weight-bandwidth bound, (1 + p) n + 2 state values per point-update."""
+    import torch
+    from oracle import nodes as onodes
+    N = 1 << log2n
+    x = torch.tensor(onodes.stretched_nodes(N), device="cuda")
+    n = 9
+    peak, src = measured_hbm_peak()
+    hmin = float((x[N // 2 + 1] - x[N // 2]).item())
+    dt = 0.3 * hmin * hmin / 0.01
+    op = L.Operator(c2=0.01)
+    out = {"workload": f"stretched grid of 2^{log2n} nodes, n = {n}, Allen-Cahn (c2 = 0.01), ETD1, dt = 0.3 h_min^2/c2",
+           "peak": peak, "peak_source": src}
+    for prec in ("mixed", "fp64"):
+        dt_ = L.state_dtype(prec)
+        es = 4 if prec == "mixed" else 8
+        W = torch.empty(N, 2, n, dtype=dt_, device="cuda")
+        hms = _timed_ms(lambda: L.lmep_harvest_nodes(h, x, n, op, dt, "etd1", W, prec))
+        u = (0.53 * x + 0.47 * torch.sin(-1.5 * torch.pi * x)).to(dt_)
+        work = torch.empty_like(u)
+        L.lmep_step_nodes(h, N, n, "etd1", "allen_cahn", dt, -1.0, 1.0, W, u, work, 2, prec)
+        ms = _timed_ms(lambda: L.lmep_step_nodes(h, N, n, "etd1", "allen_cahn", dt, -1.0, 1.0, W, u, work, K,
+                                                 prec)) / K
+        nbytes = (2 * n + 2) * es
+        gbs = nbytes * N / (ms * 1e-3) / 1e9
+        out[prec] = {"harvest_ms": hms, "harvest_nodes_per_s": N / (hms * 1e-3), "point_updates_per_s": N / (ms * 1e-3),
+                     "ms_per_step": ms, "GB_s": gbs, "frac": gbs / peak, "bytes_per_point_update": nbytes}
+        del W, u, work
+    L.lmep_sync_status(h)
+    return out
+
+
+def cfg_one_sided(L, h):
+    """Sec. 4.1: fully upwind windows at nu = (n+1)/2 - 1/2 carry a Gaussian 100 periods around [-1, 1)
+    (N = 256): error against the exact solution, and the GPU time to a fixed final time on a 2^24-point
+    grid, whose step count falls as 1/nu while a step's cost stays the same (the flat-in-n claim)."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    rows = []
+    for n in (5, 7, 9, 11, 13, 15):
+        p = wl.advection(N=256, n=n, sigma=0.5, periods=100)
+        g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, window_shift=p.window_shift)
+        op = L.Operator(c1=p.c1)
+        W = torch.empty(n, 1, n, dtype=torch.float64, device="cuda")
+        L.lmep_harvest_weights(h, g, op, p.dt, 0, None, W, "fp64")
+        u = torch.tensor(wl.advection_ic(p), device="cuda")
+        L.lmep_step(h, g, op, "linear", "none", p.dt, W, u, torch.empty_like(u), p.steps, "fp64")
+        err = float(np.max(np.abs(u.cpu().numpy() - wl.advection_exact(p, p.steps * p.dt))))
+        # the same Courant number on 2^24 points, to T = 64 h (a fixed distance)
+        q = wl.advection(N=1 << 24, n=n, sigma=0.5, periods=0)
+        gq = L.Grid(N=q.N, h=q.h, bc=q.bc, n=q.n, window_shift=q.window_shift)
+        Wq = torch.empty(n, 1, n, dtype=torch.float32, device="cuda")
+        L.lmep_harvest_weights(h, gq, op, q.dt, 0, None, Wq, "mixed")
+        v = torch.tensor(wl.advection_ic(q), dtype=torch.float32, device="cuda")
+        wv = torch.empty_like(v)
+        steps = int(np.ceil(64.0 / q.meta["nu"]))
+        L.lmep_step(h, gq, op, "linear", "none", q.dt, Wq, v, wv, 2, "mixed")
+        ms = _timed_ms(lambda: L.lmep_step(h, gq, op, "linear", "none", q.dt, Wq, v, wv, steps, "mixed"))
+        rows.append({"n": n, "nu": p.meta["nu"], "error_100_periods_N256": err, "steps_to_T": steps,
+                     "ms_to_T_N2e24": ms, "ms_per_step": ms / steps})
+        del v, wv
+    L.lmep_sync_status(h)
+    return {"workload": "u_t + u_x = 0, IC exp(-40 x^2), fully upwind windows, nu = (n+1)/2 - 1/2; error after 100 "
+                        "periods at N = 256 (FP64), time to T = 64 h at N = 2^24 (FP32)", "rows": rows}
+
+
+def other_configs(L) -> dict:
+    """Every other configuration in one pass (each leg with its own timer; a failing leg reports its error)."""
+    h = L.Handle()
+    out = {}
+    legs = (("config1_advection_diffusion", lambda: cfg1_advection_diffusion(L, h)),
+            ("config3_allen_cahn_batch", lambda: cfg3_allen_cahn(L)),
+            ("config4_kdv", lambda: cfg4_kdv(L, h)),
+            ("config5_adjoint_reduced", lambda: cfg5_adjoint(L)),
+            ("apply_sweep", lambda: cfg_apply_sweep(L, h)),
+            ("etdrk4_burgers", lambda: cfg_etdrk4(L, h)),
+            ("nonuniform_grid", lambda: cfg_nonuniform(L, h)),
+            ("one_sided_advection", lambda: cfg_one_sided(L, h)))
+    for name, fn in legs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:  # a leg that fails is reported, the others still run
+            out[name] = {"failed": repr(e)[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 2)
+    h.close()
+    return out
+
+
 # ------------------------------------------------------------------ small cases for ncu captures
 def profile_case(args) -> None:
     """Small fixed cases for `ncu -k <kernel> -s <warm-up launches> -c <count>` captures:
@@ -916,13 +1243,19 @@ def profile_case(args) -> None:
     frozen [n cfl]   four warm-up launches of the single-instance fused frozen-velocity step
                      (N = 65536, nu = 1e-6, departure-centred; FP32 form and FP64 alternately), then one
                      FP32-form and one FP64 step (`-k regex:k_warp -s 4 -c 2`).
-    set              the nine-instance Burgers set of the benchmark (FP32 form, launch shape 256 x 2):
-                     three warm-up steps, then one (`-k regex:k_frozen_set -s 6 -c 2`: the lean launch
-                     and the fallback launch of the fourth step).
+    set [block ppt]  the nine-instance Burgers set of the benchmark (FP32 form, launch shape 128 x 1 by
+                     default): the setup launch, three warm-up steps, then one
+                     (`-k regex:k_frozen_set -s 7 -c 2`: the lean and the fallback launch of the fourth
+                     step).
     adj [auto|pade]  one warm-up reverse step, then one, of the Burgers adjoint (N = 262144, n = 9, CFL 2,
                      FP32 state; `-k regex:k_adjoint_fact -s 1 -c 1` or `-k regex:k_adjoint_points ...`).
     ac [tile block]  the 4096-instance Allen-Cahn ETDRK2 batch: three warm-up steps, then one
-                     (`-k regex:k_apply -s 3 -c 1`)."""
+                     (`-k regex:k_apply -s 3 -c 1`).
+    rk4 [prec]       ETDRK4 on the viscous Burgers benchmark (N = 2^22, n = 13, FP32 by default): two
+                     warm-up steps, then one (`-k regex:k_apply_rk4 -s 2 -c 1`).
+    nodes [prec]     a stretched grid of 2^21 nodes (n = 9, Allen-Cahn ETD1, FP32 by default): the
+                     per-node harvest, two warm-up steps, then one (`-k regex:k_apply_pw -s 2 -c 1`;
+                     the harvest is the one k_warp launch)."""
     import torch
 
     import paper_2603_15964_gb300 as L
@@ -950,7 +1283,9 @@ def profile_case(args) -> None:
         insts = instances(0)
         fis = [FrozenInstance(L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=True),
                               L.Operator(c2=p.c2, frozen_adv=1.0), p.dt) for _, _, p in insts]
-        fs = FrozenSet(fis, precision="mixed", block=256, points_per_thread=2)
+        block = int(rest[0]) if rest else 128
+        ppt = int(rest[1]) if len(rest) > 1 else 1
+        fs = FrozenSet(fis, precision="mixed", block=block, points_per_thread=ppt)
         fs.load([wl.burgers_ic(N_POINTS, 0)] * len(fis))
         fs.step(4)
         L.lmep_sync_status(fs.handle)
@@ -982,6 +1317,31 @@ def profile_case(args) -> None:
         for t in range(4):
             L.lmep_step_batched_once(prob.handle, prob.workspace, u if t % 2 == 0 else w, w if t % 2 == 0 else u)
         L.lmep_sync_status(prob.handle)
+    elif case == "rk4":
+        prec = rest[0] if rest else "mixed"
+        p = wl.burgers_etd(N=1 << 22, n=13, nu=0.03, dt=0.0, steps=3)
+        p = p.with_(dt=0.5 * p.h * p.h / p.c2)
+        g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n)
+        op = L.Operator(c2=p.c2)
+        h = L.Handle()
+        W = torch.empty(p.n, 6, p.n, dtype=L.state_dtype(prec), device="cuda")
+        L.lmep_harvest_scheme_weights(h, g, op, p.dt, "etdrk4", W, prec)
+        u = torch.tensor(wl.burgers_etd_ic(p), dtype=L.state_dtype(prec), device="cuda")
+        L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, torch.empty_like(u), 3, prec)
+        L.lmep_sync_status(h)
+    elif case == "nodes":
+        from oracle import nodes as onodes
+        prec = rest[0] if rest else "mixed"
+        N, n = 1 << 21, 9
+        x = torch.tensor(onodes.stretched_nodes(N), device="cuda")
+        hmin = float((x[N // 2 + 1] - x[N // 2]).item())
+        dt = 0.3 * hmin * hmin / 0.01
+        h = L.Handle()
+        W = torch.empty(N, 2, n, dtype=L.state_dtype(prec), device="cuda")
+        L.lmep_harvest_nodes(h, x, n, L.Operator(c2=0.01), dt, "etd1", W, prec)
+        u = (0.53 * x + 0.47 * torch.sin(-1.5 * torch.pi * x)).to(L.state_dtype(prec))
+        L.lmep_step_nodes(h, N, n, "etd1", "allen_cahn", dt, -1.0, 1.0, W, u, torch.empty_like(u), 3, prec)
+        L.lmep_sync_status(h)
     else:
         raise SystemExit(f"unknown profile case {case!r}")
     torch.cuda.synchronize()
@@ -1006,9 +1366,12 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
     ap.add_argument("--adj-batch", type=int, default=8, help="adjoint workload: Burgers instances per launch")
     ap.add_argument("--adj-steps", type=int, default=4, help="adjoint workload: forward + reverse steps timed")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="Burgers workload: skip the other configurations' legs (`configs` key)")
     ap.add_argument("--profile-case", nargs="+", default=None,
                     help="run one small fixed case for an ncu capture instead of the benchmark "
-                         "(frozen [n cfl] | set | adj [auto|pade] | ac [tile block])")
+                         "(frozen [n cfl] | set [block ppt] | adj [auto|pade] | ac [tile block] | rk4 [prec] | "
+                         "nodes [prec])")
     args = ap.parse_args()
     if args.profile_case:
         return profile_case(args)
@@ -1146,6 +1509,9 @@ def main():
                                       "the product type, 1 finite series in FP64, 3..13 Pade degree; s squarings",
                             "fp32_form": m["stats"]},
     }
+    if world == 1 and not args.headline_only:
+        import paper_2603_15964_gb300 as L
+        line["configs"] = other_configs(L)
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch

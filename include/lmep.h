@@ -58,8 +58,10 @@ typedef enum {
 
 typedef enum { LMEP_BC_PERIODIC = 0, LMEP_BC_DIRICHLET = 1, LMEP_BC_NEUMANN = 2 } lmep_bc;
 typedef enum { LMEP_PREC_FP64 = 0, LMEP_PREC_MIXED = 1 } lmep_precision;
-typedef enum { LMEP_SCHEME_LINEAR = 0, LMEP_SCHEME_ETD1 = 1, LMEP_SCHEME_ETDRK2 = 2 } lmep_scheme;
-typedef enum { LMEP_N_NONE = 0, LMEP_N_ALLEN_CAHN = 1, LMEP_N_KDV = 2 } lmep_nonlin;
+typedef enum { LMEP_SCHEME_LINEAR = 0, LMEP_SCHEME_ETD1 = 1, LMEP_SCHEME_ETDRK2 = 2, LMEP_SCHEME_ETDRK4 = 3 } lmep_scheme;
+/* N(u): Allen-Cahn u - u^3; KdV -6 u u_x; Burgers -u u_x (u_x from the row of
+ * D^(1) of the point's window, Sec. 4.3.1 and 4.3.2) */
+typedef enum { LMEP_N_NONE = 0, LMEP_N_ALLEN_CAHN = 1, LMEP_N_KDV = 2, LMEP_N_BURGERS = 3 } lmep_nonlin;
 typedef enum { LMEP_EXPM_AUTO = 0, LMEP_EXPM_PADE = 1, LMEP_EXPM_SERIES = 2 } lmep_expm_method;
 
 /* Uniform 1-D grid and stencil (Sec. 2.1 step 1).
@@ -76,7 +78,14 @@ typedef enum { LMEP_EXPM_AUTO = 0, LMEP_EXPM_PADE = 1, LMEP_EXPM_SERIES = 2 } lm
  *  batch  number of independent instances of this grid stored back to back
  *         (state arrays hold batch * N values; 0 means 1).  Honoured by the
  *         frozen-velocity step and harvest, lmep_frozen_stats and
- *         lmep_adjoint_step; the other calls require batch <= 1. */
+ *         lmep_adjoint_step; the other calls require batch <= 1.
+ *  window_shift  constant-coefficient stepping with the linear scheme only
+ *         (Sec. 4.1's one-sided stencils): every window is shifted upstream
+ *         by k = window_shift nodes, |k| <= (n-1)/2, and point i takes row
+ *         class (n-1)/2 + k of its window (start i - (n-1)/2 - k; Dirichlet:
+ *         clamped into the domain).  k = (n-1)/2 is the fully upwind window
+ *         for a positive speed.  0 elsewhere.
+ *  reserved  must be 0. */
 typedef struct lmep_grid {
   int64_t N;
   double h;
@@ -84,6 +93,8 @@ typedef struct lmep_grid {
   int32_t n;
   int32_t departure_centring;
   int32_t batch;
+  int32_t window_shift;
+  int32_t reserved;
   double bc_lo, bc_hi;
 } lmep_grid;
 
@@ -124,7 +135,8 @@ LMEP_API lmep_status lmep_expm(lmep_handle* h, const double* A_dev, int64_t P, i
                       int32_t precision, int32_t* ms_dev, void* stream);
 
 /* (a1)-(a5): harvest weight rows.
- *  u_frozen_dev == NULL: constant coefficients; W_dev receives [n][1+n_phi][n]:
+ *  u_frozen_dev == NULL: constant coefficients; W_dev receives [n][1+n_phi][n]
+ *      (0 <= n_phi <= 3, n + n_phi <= 16):
  *      W[r][k][:] = row r of dt^k phi_k(dt L) (k = 0: exp(dt L)) for every row class r.
  *  u_frozen_dev != NULL: frozen velocity (requires n_phi == 0): W_dev receives
  *      [batch][N][1][n], the weights of point i on its own window (zeros at Dirichlet walls).
@@ -134,13 +146,31 @@ LMEP_API lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, co
                                  double dt, int32_t n_phi, const void* u_frozen_dev, void* W_dev,
                                  int32_t precision, void* stream);
 
+/* The weights lmep_step reads for a scheme, harvested once for a
+ * constant-coefficient problem (Sec. 2.1 step 3, Sec. 3.1 step 2):
+ *  linear, ETD1, ETDRK2: [n][1+s][n] (s = 0, 1, 2), exactly lmep_harvest_weights
+ *      with n_phi = s;
+ *  ETDRK4 (Sec. 3): [n][6][n], per row class r the rows of exp(dt L), dt alpha,
+ *      dt beta, dt gamma (alpha = phi_1 - 3 phi_2 + 4 phi_3, beta = 2 phi_2 -
+ *      4 phi_3, gamma = 4 phi_3 - phi_2 at dt L, formed in FP64 from the rows of
+ *      the augmented local matrix with p = 3), then exp(dt L / 2) and
+ *      (dt/2) phi_1(dt L / 2) (augmented, p = 1, at dt/2).  Requires n <= 13.
+ * W dtype: double for LMEP_PREC_FP64, float for LMEP_PREC_MIXED. */
+LMEP_API lmep_status lmep_harvest_scheme_weights(lmep_handle* h, const lmep_grid* g, const lmep_operator* op,
+                                                 double dt, int32_t scheme, void* W_dev, int32_t precision,
+                                                 void* stream);
+
 /* (a6) `nsteps` time steps of u in place (Sec. 3, Sec. 3.1 step 3).
- *  W_dev != NULL: stored constant-coefficient weights [n][1+n_phi][n] from
- *      lmep_harvest_weights with n_phi equal to the scheme (0 linear, 1 ETD1, 2 ETDRK2).
+ *  W_dev != NULL: stored constant-coefficient weights from
+ *      lmep_harvest_scheme_weights (linear, ETD1, ETDRK2: the same as
+ *      lmep_harvest_weights with n_phi = 0, 1, 2).
  *      Linear:  u+ = W0 u.   ETD1: u+ = W0 u + W1 N(u).
  *      ETDRK2:  a = W0 u + W1 N(u);  u+ = a + (W2 / dt)(N(a) - N(u)).
- *      N: Allen-Cahn u - u^3; KdV -6 u (D1 u) with D1 the harvest row of the
- *      first-derivative matrix on the same window.
+ *      ETDRK4:  a = E2 u + P2 N(u), b = E2 u + P2 N(a), c = E2 a + P2 (2 N(b) - N(u)),
+ *               u+ = E u + A N(u) + B (N(a) + N(b)) + G N(c)  (rows as above).
+ *      N: lmep_nonlin, with D1 the harvest row of the first-derivative matrix
+ *      on the same window.  KdV and Burgers terms with ETD1/ETDRK2 need a
+ *      periodic grid; ETDRK4 takes every boundary condition.
  *  W_dev == NULL: frozen velocity: every point rebuilds and exponentiates its
  *      own operator every step ((a1)-(a6) fused); requires the linear scheme.
  *  u_dev, work_dev: state dtype of `precision`, N elements each (batch * N for
@@ -351,6 +381,38 @@ LMEP_API lmep_status lmep_set_wait_limit(lmep_handle* h, int64_t polls);
  * own bulk copies (its outputs are then incomplete), else LMEP_ERR_NONFINITE
  * if any kernel produced Inf/NaN since the last call. */
 LMEP_API lmep_status lmep_sync_status(lmep_handle* h, void* stream);
+
+/* Non-uniform grids (Sec. 4.3.3, e.g. Chebyshev nodes): every node has its
+ * own local differentiation matrices, so its weights are harvested once per
+ * node and stored.  Nodes x_dev: double[N], strictly increasing, both ends
+ * Dirichlet walls (kept at bc_lo / bc_hi and never updated).  Point i uses
+ * the window of nodes start_i .. start_i + n - 1, start_i = clamp(i - (n-1)/2,
+ * 0, N - n), harvest row i - start_i (one-sided next to the walls).  Its
+ * derivative matrices come from Fornberg's recursion on the window's nodes (in
+ * local coordinates scaled by the window's mean spacing), X_i = dt (c0 + c1 D1
+ * + c2 D2 + c3 D3), and the rows are those of lmep_harvest_scheme_weights for
+ * the scheme (1, 2, 3 or 6 rows per point), stored W_dev[N][rows][n] in the
+ * state dtype.  3 <= n <= 15 odd, n + n_phi(scheme) <= 16, N < 2^31;
+ * op->frozen_adv must be 0. */
+LMEP_API lmep_status lmep_harvest_nodes(lmep_handle* h, int64_t N, const double* x_dev, int32_t n,
+                                        const lmep_operator* op, double dt, int32_t scheme, void* W_dev,
+                                        int32_t precision, void* stream);
+/* `nsteps` steps of u in place with the stored per-node rows of
+ * lmep_harvest_nodes (same N, n, scheme, dt): linear, ETD1, ETDRK2 or ETDRK4
+ * (formulas of lmep_step), N(u) = u - u^3 (LMEP_N_ALLEN_CAHN) or none
+ * (linear scheme).  work_dev: scratch of N state values. */
+LMEP_API lmep_status lmep_step_nodes(lmep_handle* h, int64_t N, int32_t n, int32_t scheme, int32_t nonlin,
+                                     double dt, double bc_lo, double bc_hi, const void* W_dev, void* u_dev,
+                                     void* work_dev, int64_t nsteps, int32_t precision, void* stream);
+
+/* Fourier symbol of one harvested row (Sec. 4.1's spectral footprint, the
+ * amplification factor of a constant-coefficient periodic step):
+ *   G(theta_q) = sum_j w_j e^{i theta_q (j - r)},  q < M,
+ * w_dev: double[n] (e.g. row r of exp(dt L) from lmep_harvest_weights in
+ * FP64), theta_dev: double[M], G_dev: double[M][2] (real, imaginary part).
+ * |G| > 1 for some theta means the mode grows.  1 <= n <= 64, 0 <= r < n. */
+LMEP_API lmep_status lmep_amplification(const double* w_dev, int32_t n, int32_t r, const double* theta_dev,
+                                        int64_t M, double* G_dev, void* stream);
 
 /* FMA-chain microbenchmark (all SMs): *flops_out receives achieved FLOP/s
  * (2 per FMA) of FP64 (precision 0) or FP32 (precision 1) FMAs.  Synchronous. */

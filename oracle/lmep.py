@@ -13,6 +13,10 @@
       u+ = a + dt phi_2 (N(a) - N(u)),
   with phi_2 as defined in Sec. 3 (phi_2(z) = (phi_1(z) - 1)/z).  The harvested
   row is dt^2 phi_2, so the stepper divides it by dt once.
+* Constant-coefficient windows may be shifted upstream by a fixed number of
+  nodes k (``Problem.window_shift``; Sec. 4.1's one-sided stencils take
+  k = (n-1)/2): point i then uses row class (n-1)/2 + k of its window, whose
+  start is i - (n-1)/2 - k (the harvest yields every row class).
 * Exponential rows are evaluated after an exact integer re-centring (a
   reading, derived from Thm. 2 for translation-invariant windows): row r of
   exp(dt L) equals row r-k of exp(dt L') where L' has its advection speed
@@ -104,7 +108,7 @@ def nonlinear(p: Problem, u: np.ndarray, D=None) -> np.ndarray:
         coef = -6.0 if p.nonlin == "kdv" else -1.0
         out = np.zeros_like(u)
         for i in range(p.N):
-            idx, r = grid.stencil(p, i)
+            idx, r = grid.stencil(p, i, p.window_shift)
             ux = (D[1][r] @ u[idx]) / p.h
             out[i] = coef * u[i] * ux
         return out
@@ -115,7 +119,7 @@ def _banded(p: Problem, W: np.ndarray, k: int, v: np.ndarray) -> np.ndarray:
     """(sum_j W[r_i, k, j] v[idx_i[j]])_i over the updated points; zero elsewhere."""
     out = np.zeros_like(v)
     for i in grid.updated_points(p):
-        idx, r = grid.stencil(p, i)
+        idx, r = grid.stencil(p, i, p.window_shift)
         out[i] = W[r, k] @ v[idx]
     return out
 
@@ -141,7 +145,7 @@ def _banded_rows(p: Problem, R: np.ndarray, v: np.ndarray) -> np.ndarray:
     """(sum_j R[r_i, j] v[idx_i[j]])_i over the updated points; zero elsewhere."""
     out = np.zeros_like(v)
     for i in grid.updated_points(p):
-        idx, r = grid.stencil(p, i)
+        idx, r = grid.stencil(p, i, p.window_shift)
         out[i] = R[r] @ v[idx]
     return out
 

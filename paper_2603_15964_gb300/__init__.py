@@ -20,11 +20,12 @@ from . import _lib
 from ._lib import BC, EXPM, NONLIN, PREC, SCHEME, LmepError  # noqa: F401
 
 __all__ = ["Grid", "Operator", "Handle", "lmep_build_operator", "lmep_expm", "lmep_harvest_weights",
+           "lmep_harvest_scheme_weights", "scheme_rows",
            "lmep_step", "lmep_batch_workspace_bytes", "lmep_batch_prepare", "lmep_step_batched",
            "lmep_step_batched_once", "lmep_frozen_set_workspace_bytes", "lmep_frozen_set_prepare",
            "lmep_frozen_set_refresh", "lmep_frozen_set_step_once", "frozen_set_offsets",
            "lmep_adjoint_scratch_bytes", "lmep_adjoint_step", "lmep_adjoint_step_noalloc", "lmep_frozen_stats", "lmep_set_expm_method", "lmep_set_wait_limit", "lmep_sync_status",
-           "lmep_fma_peak",
+           "lmep_fma_peak", "lmep_amplification", "lmep_harvest_nodes", "lmep_step_nodes",
            "state_dtype", "LmepError"]
 
 
@@ -40,10 +41,11 @@ class Grid:
     bc_lo: float = 0.0
     bc_hi: float = 0.0
     batch: int = 1
+    window_shift: int = 0
 
     def c(self) -> _lib.LmepGrid:
         return _lib.LmepGrid(self.N, self.h, BC[self.bc], self.n, int(self.departure_centring), self.batch,
-                             self.bc_lo, self.bc_hi)
+                             self.window_shift, 0, self.bc_lo, self.bc_hi)
 
 
 @dataclass(frozen=True)
@@ -118,6 +120,17 @@ def lmep_harvest_weights(h: Handle, grid: Grid, op: Operator, dt: float, n_phi: 
                          precision: str = "fp64", stream=None) -> None:
     _lib.call("lmep_harvest_weights", h.ptr, C.byref(grid.c()), C.byref(op.c()), dt, n_phi, _ptr(u_frozen),
               _ptr(W), PREC[precision], _stream(stream))
+
+
+def scheme_rows(scheme: str) -> int:
+    """Weight rows per row class that lmep_step reads for a scheme."""
+    return {"linear": 1, "etd1": 2, "etdrk2": 3, "etdrk4": 6}[scheme]
+
+
+def lmep_harvest_scheme_weights(h: Handle, grid: Grid, op: Operator, dt: float, scheme: str, W,
+                                precision: str = "fp64", stream=None) -> None:
+    _lib.call("lmep_harvest_scheme_weights", h.ptr, C.byref(grid.c()), C.byref(op.c()), dt, SCHEME[scheme], _ptr(W),
+              PREC[precision], _stream(stream))
 
 
 def lmep_step(h: Handle, grid: Grid, op: Operator, scheme: str, nonlin: str, dt: float, W, u, work,
@@ -238,6 +251,25 @@ def lmep_set_wait_limit(h: Handle, polls: int = -1) -> None:
 
 def lmep_sync_status(h: Handle, stream=None) -> None:
     _lib.call("lmep_sync_status", h.ptr, _stream(stream))
+
+
+def lmep_harvest_nodes(h: Handle, x, n: int, op: Operator, dt: float, scheme: str, W, precision: str = "fp64",
+                       stream=None) -> None:
+    """Per-node weight rows W[N][rows][n] on the non-uniform grid x (float64 CUDA tensor, Dirichlet walls)."""
+    _lib.call("lmep_harvest_nodes", h.ptr, int(x.numel()), _ptr(x), n, C.byref(op.c()), dt, SCHEME[scheme], _ptr(W),
+              PREC[precision], _stream(stream))
+
+
+def lmep_step_nodes(h: Handle, N: int, n: int, scheme: str, nonlin: str, dt: float, bc_lo: float, bc_hi: float, W,
+                    u, work, nsteps: int, precision: str = "fp64", stream=None) -> None:
+    _lib.call("lmep_step_nodes", h.ptr, N, n, SCHEME[scheme], NONLIN[nonlin], dt, bc_lo, bc_hi, _ptr(W), _ptr(u),
+              _ptr(work), nsteps, PREC[precision], _stream(stream))
+
+
+def lmep_amplification(w, r: int, theta, G, stream=None) -> None:
+    """G[q] = sum_j w_j e^{i theta_q (j - r)} (G: float64 [M, 2], real and imaginary parts)."""
+    _lib.call("lmep_amplification", _ptr(w), int(w.numel()), int(r), _ptr(theta), int(theta.numel()), _ptr(G),
+              _stream(stream))
 
 
 def lmep_fma_peak(precision: str = "fp64") -> float:

@@ -17,15 +17,15 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "lmep.h")
 OK, ERR_INVALID, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_NOMEM = range(7)
 BC = {"periodic": 0, "dirichlet": 1, "neumann": 2}
 PREC = {"fp64": 0, "mixed": 1}
-SCHEME = {"linear": 0, "etd1": 1, "etdrk2": 2}
-NONLIN = {"none": 0, "allen_cahn": 1, "kdv": 2}
+SCHEME = {"linear": 0, "etd1": 1, "etdrk2": 2, "etdrk4": 3}
+NONLIN = {"none": 0, "allen_cahn": 1, "kdv": 2, "burgers": 3}
 EXPM = {"auto": 0, "pade": 1, "series": 2}
 
 
 class LmepGrid(C.Structure):
     _fields_ = [("N", C.c_int64), ("h", C.c_double), ("bc", C.c_int32), ("n", C.c_int32),
-                ("departure_centring", C.c_int32), ("batch", C.c_int32),
-                ("bc_lo", C.c_double), ("bc_hi", C.c_double)]
+                ("departure_centring", C.c_int32), ("batch", C.c_int32), ("window_shift", C.c_int32),
+                ("reserved", C.c_int32), ("bc_lo", C.c_double), ("bc_hi", C.c_double)]
 
 
 class LmepOperator(C.Structure):
@@ -60,6 +60,8 @@ _SIGS = {
     "lmep_expm": [_P, _P, C.c_int64, C.c_int32, _P, C.c_int32, _P, _P],
     "lmep_harvest_weights": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, C.c_int32, _P,
                              _P, C.c_int32, _P],
+    "lmep_harvest_scheme_weights": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_double, C.c_int32, _P,
+                                    C.c_int32, _P],
     "lmep_step": [_P, C.POINTER(LmepGrid), C.POINTER(LmepOperator), C.c_int32, C.c_int32, C.c_double, _P,
                   _P, _P, C.c_int64, C.c_int32, _P],
     "lmep_batch_workspace_bytes": [C.POINTER(LmepBatchDesc), C.c_int32, C.POINTER(C.c_size_t)],
@@ -80,6 +82,11 @@ _SIGS = {
     "lmep_set_wait_limit": [_P, C.c_int64],
     "lmep_sync_status": [_P, _P],
     "lmep_fma_peak": [C.c_int32, C.POINTER(C.c_double)],
+    "lmep_harvest_nodes": [_P, C.c_int64, _P, C.c_int32, C.POINTER(LmepOperator), C.c_double, C.c_int32, _P,
+                           C.c_int32, _P],
+    "lmep_step_nodes": [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double, _P,
+                        _P, _P, C.c_int64, C.c_int32, _P],
+    "lmep_amplification": [_P, C.c_int32, C.c_int32, _P, C.c_int64, _P, _P],
     "lmep_status_string": [C.c_int],
     "lmep_last_error": [],
     "lmep_version": [],

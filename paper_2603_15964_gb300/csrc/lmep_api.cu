@@ -2,6 +2,7 @@
 // status flags and the batch workspace.  All compute runs in the kernels of
 // lmep_expm.cu, lmep_apply.cu and lmep_adjoint.cu.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -70,8 +71,16 @@ lmep_status check_grid(const lmep_grid* g, int n_phi) {
   if (g->bc < 0 || g->bc > 2) return fail(LMEP_ERR_INVALID, "unknown boundary condition");
   if (g->batch < 0) return fail(LMEP_ERR_INVALID, "batch must be >= 0");
   if (g->N * (g->batch > 1 ? g->batch : 1) > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "batch * N too large");
-  if (n_phi < 0 || n_phi > 2) return fail(LMEP_ERR_INVALID, "n_phi must be 0, 1 or 2");
+  if (n_phi < 0 || n_phi > 3) return fail(LMEP_ERR_INVALID, "n_phi must be 0, 1, 2 or 3");
   if (g->n + n_phi > 16) return fail(LMEP_ERR_UNSUPPORTED, "n + n_phi must be <= 16");
+  if (g->window_shift < -(g->n - 1) / 2 || g->window_shift > (g->n - 1) / 2)
+    return fail(LMEP_ERR_INVALID, "|window_shift| must be <= (n-1)/2");
+  if (g->reserved != 0) return fail(LMEP_ERR_INVALID, "lmep_grid.reserved must be 0");
+  return LMEP_OK;
+}
+
+lmep_status no_shift(const lmep_grid* g) {
+  if (g->window_shift != 0) return fail(LMEP_ERR_UNSUPPORTED, "window_shift is for constant-coefficient linear steps");
   return LMEP_OK;
 }
 
@@ -271,6 +280,7 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
   const KParams p = make_params(g, op, dt, n_phi);
   const bool mixed = precision == LMEP_PREC_MIXED;
   if (u_frozen_dev) {
+    if ((st = no_shift(g)) != LMEP_OK) return st;
     if (n_phi != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity weights need n_phi == 0");
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen weights need N >= 2n");
     KParams pf = p;
@@ -287,12 +297,40 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
   return LMEP_OK;
 }
 
+lmep_status lmep_harvest_scheme_weights(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, double dt,
+                                        int32_t scheme, void* W_dev, int32_t precision, void* stream) {
+  if (!h || !op || !W_dev) return fail(LMEP_ERR_INVALID, "NULL handle/operator/W");
+  if (scheme < 0 || scheme > 3) return fail(LMEP_ERR_INVALID, "unknown scheme");
+  lmep_status st = check_grid(g, scheme);
+  if (st != LMEP_OK) return st;
+  if ((st = check_prec(precision)) != LMEP_OK) return st;
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
+  if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "constant-coefficient harvest takes batch <= 1");
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  if (scheme < 3) {
+    CK(lmep::launch_harvest_const(make_params(g, op, dt, scheme), nullptr, 1, W_dev, mixed, S(stream)), "harvest");
+    return LMEP_OK;
+  }
+  // ETDRK4: rows of exp(dt L), dt alpha, dt beta, dt gamma (augmented, p = 3, at dt), then
+  // exp(dt L / 2) and (dt/2) phi_1(dt L / 2) (augmented, p = 1, at dt/2): 6 rows per row class
+  KParams p = make_params(g, op, dt, 3);
+  p.w_rows = 6;
+  p.rk4 = 1;
+  CK(lmep::launch_harvest_const(p, nullptr, 1, W_dev, mixed, S(stream)), "harvest(etdrk4, dt)");
+  KParams q = make_params(g, op, 0.5 * dt, 1);
+  q.w_rows = 6;
+  q.w_row0 = 4;
+  CK(lmep::launch_harvest_const(q, nullptr, 1, W_dev, mixed, S(stream)), "harvest(etdrk4, dt/2)");
+  return LMEP_OK;
+}
+
 lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* op, int32_t scheme,
                       int32_t nonlin, double dt, const void* W_dev, void* u_dev, void* work_dev,
                       int64_t nsteps, int32_t precision, void* stream) {
   if (!h || !op) return fail(LMEP_ERR_INVALID, "NULL handle/operator");
-  if (scheme < 0 || scheme > 2) return fail(LMEP_ERR_INVALID, "unknown scheme");
-  if (nonlin < 0 || nonlin > 2) return fail(LMEP_ERR_INVALID, "unknown nonlinearity");
+  if (scheme < 0 || scheme > 3) return fail(LMEP_ERR_INVALID, "unknown scheme");
+  if (nonlin < 0 || nonlin > 3) return fail(LMEP_ERR_INVALID, "unknown nonlinearity");
   if ((scheme == 0) != (nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
   lmep_status st = check_grid(g, scheme);
   if (st != LMEP_OK) return st;
@@ -308,6 +346,7 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
   void* cur = u_dev;
   void* nxt = work_dev;
   if (!W_dev) {
+    if ((st = no_shift(g)) != LMEP_OK) return st;
     if (scheme != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity stepping uses the linear scheme");
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann frozen step needs N >= 2n");
     if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "W_dev is NULL but the operator is not frozen");
@@ -322,14 +361,34 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
   } else {
     if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
     if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "stored-weight stepping takes batch <= 1 (use lmep_batch_*)");
-    if (nonlin == 2 && g->bc != LMEP_BC_PERIODIC) return fail(LMEP_ERR_UNSUPPORTED, "KdV needs a periodic grid");
+    if (scheme != 0 && (st = no_shift(g)) != LMEP_OK) return st;
+    if (scheme == 3) {
+      // ETDRK4: the CTA-tiled four-stage kernel, every boundary condition and nonlinearity
+      const int H = lmep::rk4_halo(g->n, nonlin, g->bc);
+      if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
+      if (g->bc == LMEP_BC_PERIODIC && g->N < H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
+      for (int64_t t = 0; t < nsteps; ++t) {
+        CK(lmep::launch_apply_rk4(g->N, g->h, g->bc, g->n, nonlin, dt, g->bc_lo, g->bc_hi, cur, nxt, W_dev, mixed,
+                                  h->flags, S(stream)),
+           "step(etdrk4)");
+        std::swap(cur, nxt);
+      }
+      if (cur != u_dev)
+        CK(cudaMemcpyAsync(u_dev, cur, size_t(g->N) * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
+      return LMEP_OK;
+    }
+    if (nonlin >= 2 && g->bc != LMEP_BC_PERIODIC)
+      return fail(LMEP_ERR_UNSUPPORTED, "KdV and Burgers terms with ETD1/ETDRK2 need a periodic grid");
     // the pipelined kernel copies 16-byte aligned blocks of the state
-    const bool fast = nonlin != 2 && g->bc != LMEP_BC_DIRICHLET && aligned16(cur) && aligned16(nxt);
-    const int H = fast ? lmep::apply_fast_halo(g->n, scheme) : lmep::apply_halo(g->n, scheme, nonlin, g->bc);
+    const bool fast = nonlin < 2 && g->bc != LMEP_BC_DIRICHLET && g->window_shift == 0 && aligned16(cur) &&
+                      aligned16(nxt);
+    const int H = fast ? lmep::apply_fast_halo(g->n, scheme)
+                       : lmep::apply_halo(g->n, scheme, nonlin, g->bc) + std::abs(int(g->window_shift));
     if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
     if (g->bc == LMEP_BC_PERIODIC && g->N < H + 8) return fail(LMEP_ERR_UNSUPPORTED, "N too small for the halo");
     ApplyParams a{};
     a.halo = H;
+    a.shift = g->window_shift;
     a.fast = fast ? 1 : 0;
     a.n = g->n;
     a.scheme = scheme;
@@ -373,8 +432,10 @@ struct BatchLayout {
 lmep_status batch_layout(const lmep_batch_desc* d, int32_t precision, BatchLayout* L) {
   if (!d || d->B <= 0 || !d->N_host || !d->h_host || !d->bc_host) return fail(LMEP_ERR_INVALID, "bad batch descriptor");
   if (d->n < 3 || d->n > 15 || d->n % 2 == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15");
+  if (d->scheme == 3) return fail(LMEP_ERR_UNSUPPORTED, "ETDRK4 batches are not supported (use lmep_step)");
   if (d->scheme < 0 || d->scheme > 2 || d->n + d->scheme > 16) return fail(LMEP_ERR_INVALID, "bad scheme");
-  if (d->nonlin == 2) return fail(LMEP_ERR_UNSUPPORTED, "KdV batches are not supported");
+  if (d->nonlin < 0 || d->nonlin > 3) return fail(LMEP_ERR_INVALID, "unknown nonlinearity");
+  if (d->nonlin >= 2) return fail(LMEP_ERR_UNSUPPORTED, "KdV and Burgers batches are not supported");
   if ((d->scheme == 0) != (d->nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
   if (d->op.frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "batches use constant operators");
   lmep_status st = check_prec(precision);
@@ -560,6 +621,7 @@ lmep_status set_layout(const lmep_frozen_set_desc* d, int32_t precision, int32_t
     const lmep_operator* op = d->ops_host + b;
     const double dt = d->dt_host[b];
     if ((st = check_grid(g, 0)) != LMEP_OK) return st;
+    if ((st = no_shift(g)) != LMEP_OK) return st;
     if (g->batch > 1) return fail(LMEP_ERR_INVALID, "frozen-set instances take batch <= 1");
     if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "frozen-set instances need a frozen operator");
     if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
@@ -643,6 +705,7 @@ lmep_status lmep_adjoint_step(lmep_handle* h, const lmep_grid* g, const lmep_ope
   if (st != LMEP_OK) return st;
   st = check_prec(precision);
   if (st != LMEP_OK) return st;
+  if ((st = no_shift(g)) != LMEP_OK) return st;
   if (g->bc == LMEP_BC_NEUMANN) return fail(LMEP_ERR_UNSUPPORTED, "adjoint supports periodic and Dirichlet grids");
   if (g->bc == LMEP_BC_PERIODIC && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "periodic adjoint needs N >= 2n");
   if (!u_dev || !lam_next_dev || !lam_dev || !dnu_dev || !scratch_dev) return fail(LMEP_ERR_INVALID, "NULL buffer");
@@ -665,6 +728,7 @@ lmep_status lmep_frozen_stats(lmep_handle* h, const lmep_grid* g, const lmep_ope
   if (st != LMEP_OK) return st;
   st = check_prec(precision);
   if (st != LMEP_OK) return st;
+  if ((st = no_shift(g)) != LMEP_OK) return st;
   if (op->frozen_adv == 0.0) return fail(LMEP_ERR_INVALID, "lmep_frozen_stats needs a frozen operator");
   if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
   if (g->bc == LMEP_BC_NEUMANN && g->N < 2 * g->n) return fail(LMEP_ERR_UNSUPPORTED, "Neumann needs N >= 2n");
@@ -702,6 +766,81 @@ lmep_status lmep_sync_status(lmep_handle* h, void* stream) {
     if (flags & 2u) return fail(LMEP_ERR_TIMEOUT, "a kernel gave up waiting for a bulk copy");
     return fail(LMEP_ERR_NONFINITE, "a kernel produced a non-finite value");
   }
+  return LMEP_OK;
+}
+
+// ------------------------------------------------------------------ non-uniform grids
+namespace {
+lmep_status check_nodes(int64_t N, int32_t n, int32_t scheme, int32_t precision) {
+  if (n < 3 || n > 15 || n % 2 == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15");
+  if (N < n) return fail(LMEP_ERR_INVALID, "N must be >= n");
+  if (N >= (int64_t(1) << 31)) return fail(LMEP_ERR_UNSUPPORTED, "non-uniform grids take N < 2^31");
+  if (scheme < 0 || scheme > 3) return fail(LMEP_ERR_INVALID, "unknown scheme");
+  if (n + scheme > 16) return fail(LMEP_ERR_UNSUPPORTED, "n + n_phi must be <= 16");
+  return check_prec(precision);
+}
+}  // namespace
+
+lmep_status lmep_harvest_nodes(lmep_handle* h, int64_t N, const double* x_dev, int32_t n, const lmep_operator* op,
+                               double dt, int32_t scheme, void* W_dev, int32_t precision, void* stream) {
+  if (!h || !op || !x_dev || !W_dev) return fail(LMEP_ERR_INVALID, "NULL handle/operator/nodes/W");
+  lmep_status st = check_nodes(N, n, scheme, precision);
+  if (st != LMEP_OK) return st;
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  if (op->frozen_adv != 0.0) return fail(LMEP_ERR_INVALID, "stored weights need a constant operator");
+  lmep_grid g{};
+  g.N = N;
+  g.h = 1.0;
+  g.bc = LMEP_BC_DIRICHLET;
+  g.n = n;
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  const int R = lmep::pw_rows(scheme);
+  KParams p = make_params(&g, op, dt, scheme);
+  p.w_rows = R;
+  p.rk4 = scheme == 3;
+  CK(lmep::launch_harvest_nodes(p, x_dev, W_dev, mixed, S(stream)), "harvest_nodes");
+  if (scheme == 3) {
+    KParams q = make_params(&g, op, 0.5 * dt, 1);
+    q.w_rows = R;
+    q.w_row0 = 4;
+    CK(lmep::launch_harvest_nodes(q, x_dev, W_dev, mixed, S(stream)), "harvest_nodes(dt/2)");
+  }
+  return LMEP_OK;
+}
+
+lmep_status lmep_step_nodes(lmep_handle* h, int64_t N, int32_t n, int32_t scheme, int32_t nonlin, double dt,
+                            double bc_lo, double bc_hi, const void* W_dev, void* u_dev, void* work_dev, int64_t nsteps,
+                            int32_t precision, void* stream) {
+  if (!h || !W_dev || !u_dev || !work_dev) return fail(LMEP_ERR_INVALID, "NULL argument");
+  lmep_status st = check_nodes(N, n, scheme, precision);
+  if (st != LMEP_OK) return st;
+  if (nonlin != LMEP_N_NONE && nonlin != LMEP_N_ALLEN_CAHN)
+    return fail(LMEP_ERR_UNSUPPORTED, "non-uniform grids take a pointwise nonlinearity (Allen-Cahn) or none");
+  if ((scheme == 0) != (nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
+  if (u_dev == work_dev) return fail(LMEP_ERR_INVALID, "u_dev and work_dev must differ");
+  if (nsteps < 0) return fail(LMEP_ERR_INVALID, "nsteps < 0");
+  if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
+  const bool mixed = precision == LMEP_PREC_MIXED;
+  void* cur = u_dev;
+  void* nxt = work_dev;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    CK(lmep::launch_apply_pw(N, n, scheme, nonlin, dt, bc_lo, bc_hi, cur, nxt, W_dev, mixed, h->flags, S(stream)),
+       "step_nodes");
+    std::swap(cur, nxt);
+  }
+  if (cur != u_dev)
+    CK(cudaMemcpyAsync(u_dev, cur, size_t(N) * (mixed ? 4 : 8), cudaMemcpyDeviceToDevice, S(stream)), "copy");
+  return LMEP_OK;
+}
+
+lmep_status lmep_amplification(const double* w_dev, int32_t n, int32_t r, const double* theta_dev, int64_t M,
+                               double* G_dev, void* stream) {
+  if (n < 1 || n > 64) return fail(LMEP_ERR_INVALID, "n must be 1..64");
+  if (r < 0 || r >= n) return fail(LMEP_ERR_INVALID, "r must be in [0, n)");
+  if (M < 0) return fail(LMEP_ERR_INVALID, "M < 0");
+  if (M == 0) return LMEP_OK;
+  if (!w_dev || !theta_dev || !G_dev) return fail(LMEP_ERR_INVALID, "NULL buffer");
+  CK(lmep::launch_symbol(w_dev, n, r, theta_dev, M, G_dev, S(stream)), "amplification");
   return LMEP_OK;
 }
 

@@ -96,6 +96,32 @@ __device__ inline void fornberg_row(double z, int n, double c[4][DMAX]) {
   }
 }
 
+// The same recursion on arbitrary distinct nodes xs[0..n-1] (non-uniform
+// windows, Sec. 4.3.3): c[k][j] are the weights of d^k/dx^k at z.
+__device__ inline void fornberg_row_nodes(double z, const double* xs, int n, double c[4][DMAX]) {
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < DMAX; ++j) c[k][j] = 0.0;
+  c[0][0] = 1.0;
+  double c1 = 1.0, c4 = xs[0] - z;
+  for (int i = 1; i < n; ++i) {
+    const int mn = i < 3 ? i : 3;
+    double c2 = 1.0;
+    const double c5 = c4;
+    c4 = xs[i] - z;
+    for (int j = 0; j < i; ++j) {
+      const double c3 = xs[i] - xs[j];
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int k = mn; k >= 1; --k) c[k][i] = c1 * (k * c[k - 1][i - 1] - c5 * c[k][i - 1]) / c2;
+        c[0][i] = -c1 * c5 * c[0][i - 1] / c2;
+      }
+      for (int k = mn; k >= 1; --k) c[k][j] = (c4 * c[k][j] - k * c[k - 1][j]) / c3;
+      c[0][j] = c4 * c[0][j] / c3;
+    }
+    c1 = c2;
+  }
+}
+
 // Fill Dh[k-1][i*LD + j] = h^k D^(k)[i][j] (k = 1..3) for the uniform window of
 // width n in shared memory.  Threads 0..n-1 of the block each build one row.
 // Caller synchronises.

@@ -202,6 +202,17 @@ cudaError_t launch_harvest_const(const KParams& p, const double* h_inst, int64_t
   return mixed ? warp_job_f32(p.n + p.n_phi, job, s) : warp_job_f64(p.n + p.n_phi, job, s);
 }
 
+cudaError_t launch_harvest_nodes(const KParams& p, const double* x, void* W, bool mixed, cudaStream_t s) {
+  if (p.N <= 0) return cudaSuccess;
+  WarpJob job{};
+  job.mode = MODE_NODES;
+  job.p = p;
+  job.items = p.N;
+  job.x = x;
+  job.out = W;
+  return mixed ? warp_job_f32(p.n + p.n_phi, job, s) : warp_job_f64(p.n + p.n_phi, job, s);
+}
+
 // exp(E) of the point-independent part E = c2h Dh2 + c3h Dh3 of a
 // frozen-velocity local matrix: one warp, FP64 Pade scaling and squaring,
 // row-major D x D into out; then Dh2 exp(E) (D x D) into out2, the direction

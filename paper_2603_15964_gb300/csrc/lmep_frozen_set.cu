@@ -94,6 +94,30 @@ cudaError_t allow_smem(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
+
+// The lean kernel of a set and its shared memory: two staging buffers (table, tile and halo).
+template <typename PT>
+auto set_kernel(int ppt) { return ppt == 2 ? k_frozen_set<PT, 2> : k_frozen_set<PT, 1>; }
+template <typename PT>
+size_t set_smem(const SetLayout& L) {
+  return 2 * (size_t(TAB_MAX) + size_t(L.block) * L.ppt + 2 * DMAX) * sizeof(PT);
+}
+// Persistent grid: every CTA that fits on the device at once (at most one per tile).
+template <typename PT>
+cudaError_t set_grid(SetLayout& L) {
+  auto kern = set_kernel<PT>(L.ppt);
+  const size_t smem = set_smem<PT>(L);
+  cudaError_t e = allow_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.block, smem)) != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int64_t cap = int64_t(device_info().sms) * per_sm;
+  L.grid = int(L.ntiles < cap ? L.ntiles : cap);
+  return cudaSuccess;
+}
+
+
 }  // namespace
 
 SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int block, int ppt, bool mixed) {
@@ -117,19 +141,21 @@ SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int b
   L.inst = align256(L.ok + size_t(B) * 4);
   L.jobs = align256(L.inst + size_t(B) * sizeof(SetInst));
   L.tiles = align256(L.jobs + size_t(B) * sizeof(WarpJob));
-  L.exps = align256(L.tiles + size_t(tiles) * sizeof(int2));
+  L.exps = align256(L.tiles + size_t(tiles) * sizeof(SetTile));
   L.tab = align256(L.exps + size_t(B) * 2 * DMAX * DMAX * 8);
   L.lists = align256(L.tab + size_t(tabn) * es);
   L.total = align256(L.lists + size_t(points) * 4);
   return L;
 }
 
-cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, const int32_t* route,
+cudaError_t frozen_set_prepare(void* ws, SetLayout& L, const KParams* p, const int32_t* route,
                                const int64_t* offsets, cudaStream_t s) {
+  cudaError_t e0 = L.mixed ? set_grid<float>(L) : set_grid<double>(L);
+  if (e0 != cudaSuccess) return e0;
   char* base = static_cast<char*>(ws);
   std::vector<SetInst> inst(size_t(L.B));
   std::vector<WarpJob> jobs(size_t(L.B));
-  std::vector<int2> tiles;
+  std::vector<SetTile> tiles;
   tiles.reserve(size_t(L.ntiles));
   int64_t list_off = 0, tab = 0;
   const int64_t tp = int64_t(L.block) * L.ppt;
@@ -156,7 +182,17 @@ cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, c
   for (int64_t b = 0; b < L.B; ++b) order[size_t(b)] = b;
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return p[x].n > p[y].n; });
   for (int64_t b : order)
-    for (int64_t t0 = 0; t0 < p[b].N; t0 += tp) tiles.push_back(make_int2(int(b), int(t0)));
+    for (int64_t t0 = 0; t0 < p[b].N; t0 += tp) {
+      SetTile t{};
+      t.off = inst[size_t(b)].off;
+      t.N = int32_t(p[b].N);
+      t.t0 = int32_t(t0);
+      t.b = int32_t(b);
+      t.n = p[b].n;
+      t.bc = p[b].bc;
+      t.tab = int32_t(inst[size_t(b)].tab);
+      tiles.push_back(t);
+    }
   cudaError_t e;
   if ((e = cudaMemsetAsync(base + L.ctl, 0, size_t(L.B + 1) * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(base + L.inst, inst.data(), inst.size() * sizeof(SetInst), cudaMemcpyHostToDevice, s)) !=
@@ -165,7 +201,7 @@ cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, c
   if ((e = cudaMemcpyAsync(base + L.jobs, jobs.data(), jobs.size() * sizeof(WarpJob), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
-  if ((e = cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, s)) !=
+  if ((e = cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(SetTile), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
   if ((e = frozen_set_refresh(ws, L, s)) != cudaSuccess) return e;
@@ -197,7 +233,8 @@ template <typename PT>
 cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_out, unsigned* flags, cudaStream_t s) {
   SetArgs a;
   a.inst = reinterpret_cast<const SetInst*>(base + L.inst);
-  a.tiles = reinterpret_cast<const int2*>(base + L.tiles);
+  a.tiles = reinterpret_cast<const SetTile*>(base + L.tiles);
+  a.ntiles = L.ntiles;
   a.tab = base + L.tab;
   a.ok = reinterpret_cast<const int32_t*>(base + L.ok);
   a.fail_count = reinterpret_cast<int32_t*>(base + L.ctl);
@@ -205,16 +242,10 @@ cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_o
   a.u = u_in;
   a.out = u_out;
   a.flags = flags;
-  const size_t smem = (size_t(TAB_MAX) + size_t(L.block) * L.ppt + 2 * DMAX) * sizeof(PT);
   cudaError_t e;
-  if (L.ppt == 2) {
-    if ((e = allow_smem(k_frozen_set<PT, 2>, smem)) != cudaSuccess) return e;
-    k_frozen_set<PT, 2><<<unsigned(L.ntiles), L.block, smem, s>>>(a);
-  } else {
-    if ((e = allow_smem(k_frozen_set<PT, 1>, smem)) != cudaSuccess) return e;
-    k_frozen_set<PT, 1><<<unsigned(L.ntiles), L.block, smem, s>>>(a);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_pdl(set_kernel<PT>(L.ppt), unsigned(L.grid), unsigned(L.block), set_smem<PT>(L), s, a)) !=
+      cudaSuccess)
+    return e;
   FbArgs f;
   f.inst = a.inst;
   f.jobs = reinterpret_cast<const WarpJob*>(base + L.jobs);
@@ -225,8 +256,8 @@ cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_o
   f.u = u_in;
   f.out = u_out;
   f.flags = flags;
-  const unsigned grid = unsigned(device_info().sms);
-  return sizeof(PT) == 4 ? launch_set_fallback_f32(f, grid, s) : launch_set_fallback_f64(f, grid, s);
+  const unsigned fgrid = unsigned(device_info().sms);
+  return sizeof(PT) == 4 ? launch_set_fallback_f32(f, fgrid, s) : launch_set_fallback_f64(f, fgrid, s);
 }
 }  // namespace
 

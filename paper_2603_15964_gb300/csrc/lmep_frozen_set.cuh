@@ -24,9 +24,18 @@ __host__ __device__ constexpr int tab_np(int n) { return (n + 3) / 4 * 4; }
 __host__ __device__ constexpr int tab_elems(int n) { return (n + 1) * tab_np(n); }
 constexpr int TAB_MAX = (DMAX + 1) * DMAX;
 
+// Per-tile record: what staging a tile needs before its instance record has
+// arrived (the kernel loads these two tiles ahead).
+struct alignas(16) SetTile {
+  int64_t off;                    // first state element of the instance
+  int32_t N, t0, b, n, bc, tab;   // instance size, first point, instance, width, boundary, table offset
+};
+static_assert(sizeof(SetTile) == 32, "SetTile is 32 bytes");
+
 struct SetArgs {
   const SetInst* inst;
-  const int2* tiles;  // {instance, first point}
+  const SetTile* tiles;
+  int64_t ntiles;
   const void* tab;
   const int32_t* ok;  // per instance: 1 when its exp(E) table is finite
   int32_t* fail_count;
@@ -69,33 +78,83 @@ __device__ __forceinline__ void load_row(const T* src, T (&row)[NP]) {
   }
 }
 
-// One tile of instance b: points t0 .. t0 + min(block * PPT, N - t0) - 1, thread
-// t taking points t0 + t + k * blockDim.x (k < PPT).  The arithmetic of a point
-// is that of the factorised stage of frozen_chunk (same operations in the same
-// order), so both paths give the same bits.
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic
+// stream serialization may start while the previous kernel of the stream is
+// finishing; griddepcontrol.wait returns once that kernel has completed and
+// its memory is visible (at once for an ordinary launch), and
+// griddepcontrol.launch_dependents lets the next kernel start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Window start of point i with shift k (window_start in 32-bit integers:
+// instances of a set have N < 2^31).
+__device__ __forceinline__ int set_window_start(int i, int N, int n, int bc, int k) {
+  int s = i - ((n - 1) >> 1) - k;
+  if (bc == BC_DIRICHLET) s = s < 0 ? 0 : (s > N - n ? N - n : s);
+  return s;
+}
+
+// Issue the asynchronous copies that stage tile d in shared memory: its
+// instance record, the instance's exp(E) table and the tile's values with
+// n - 1 more on each side (one wrap for periodic, N >= n; one reflection for
+// Neumann, N >= 2n; Dirichlet windows stay inside [0, N), outside values are 0).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return unsigned(__cvta_generic_to_shared(p)); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <typename PT>
+__device__ __forceinline__ void stage_tile(const SetArgs& a, const SetTile& d, SetInst* s_in, PT* sT, PT* su, int tp) {
+  constexpr int NI = int(sizeof(SetInst)) / 16;
+  for (int e = threadIdx.x; e < NI; e += blockDim.x)
+    cp_async<16>(reinterpret_cast<int4*>(s_in) + e, reinterpret_cast<const int4*>(a.inst + d.b) + e);
+  constexpr int PER16 = 16 / int(sizeof(PT));
+  const PT* tab = static_cast<const PT*>(a.tab) + d.tab;
+  const int tel = (d.n + 1) * ((d.n + 3) / 4 * 4);
+  for (int e = threadIdx.x; e < tel / PER16; e += blockDim.x) cp_async<16>(sT + e * PER16, tab + e * PER16);
+  const int H = d.n - 1;
+  const int N = d.N;
+  const int len = N - d.t0 < tp ? N - d.t0 : tp;
+  const PT* u = static_cast<const PT*>(a.u) + d.off;
+  for (int q = threadIdx.x; q < len + 2 * H; q += blockDim.x) {
+    int i = d.t0 - H + q;
+    bool have = true;
+    if (d.bc == BC_PERIODIC) {
+      i = i < 0 ? i + N : (i >= N ? i - N : i);
+    } else if (d.bc == BC_NEUMANN) {
+      i = i < 0 ? -i : i;
+      i = i > N - 1 ? 2 * (N - 1) - i : i;
+    } else {
+      have = i >= 0 && i < N;
+    }
+    if (have) cp_async<int(sizeof(PT))>(su + q, u + i);
+    else su[q] = PT(0);
+  }
+}
+
+// The points of one staged tile of instance b: points t0 .. t0 + min(block * PPT,
+// N - t0) - 1, thread t taking points t0 + t + k * blockDim.x (k < PPT).  The
+// arithmetic of a point is that of the factorised stage of frozen_chunk (same
+// operations in the same order), so both paths give the same bits.
 template <int D, typename PT, int PPT>
-__device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, int b, int64_t t0, PT* sT, PT* su,
-                                         unsigned& bad) {
+__device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, int b, int t0, const PT* sT,
+                                         const PT* su, unsigned& bad) {
   using ST = PT;
   constexpr bool F32 = sizeof(PT) == 4;
   constexpr int H = D - 1;  // a window lies within [i - (n - 1), i + n - 1]
   constexpr int NP = tab_np(D);
   const KParams& p = in.p;
-  const int64_t N = p.N;
+  const int N = int(p.N);
   const int bc = p.bc;
   const int tp = int(blockDim.x) * PPT;
-  const int len = int(N - t0 < int64_t(tp) ? N - t0 : int64_t(tp));
-  const ST* u = static_cast<const ST*>(a.u) + in.off;
+  const int len = N - t0 < tp ? N - t0 : tp;
   ST* out = static_cast<ST*>(a.out) + in.off;
-  const ST* tab = static_cast<const ST*>(a.tab) + in.tab;
-  for (int e = threadIdx.x; e < tab_elems(D); e += blockDim.x) sT[e] = tab[e];
-  for (int q = threadIdx.x; q < len + 2 * H; q += blockDim.x) {
-    const int64_t i = t0 - H + q;
-    ST v = ST(0);
-    if (bc != BC_DIRICHLET || (i >= 0 && i < N)) v = u[grid_index(i, N, bc)];
-    su[q] = v;
-  }
-  __syncthreads();
   const bool fact = in.route == 0 && a.ok[b] != 0;
   PT l[PPT][D];
   int ls[PPT];
@@ -104,16 +163,16 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
   for (int k = 0; k < PPT; ++k) {
     const int q = int(threadIdx.x) + k * int(blockDim.x);
     vld[k] = q < len;
-    const int64_t i = t0 + (vld[k] ? q : 0);
+    const int i = t0 + (vld[k] ? q : 0);
     const bool wall = bc == BC_DIRICHLET && (i == 0 || i == N - 1);
     live[k] = vld[k] && !wall;
-    int64_t st;
+    int st;
     if constexpr (F32) {
       // in FP32 but for the window's integer decision next to a tie (exact FP64 test)
       const float uf = live[k] ? float(su[q + H]) : 0.0f;
       const int kd = p.dep ? departure_shift_f32(uf, p, D) : 0;
-      st = window_start(i, N, D, bc, kd);
-      const int r = int(i - st);
+      st = set_window_start(i, N, D, bc, kd);
+      const int r = i - st;
       const float a1 = p.c1_f - p.fa_f * uf;
       const int kr = int(fmaxf(float(r - (D - 1)), fminf(float(r), floorf(fmaf(-a1, p.dt_h_f, 0.5f)))));
       const float c1f = fmaf(a1, p.dt_h_f, float(kr));
@@ -121,14 +180,14 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
     } else {
       const double ui = live[k] ? double(su[q + H]) : 0.0;
       const int kd = p.dep ? departure_shift(ui, p.dt, p.h, D, p.dt_h) : 0;
-      st = window_start(i, N, D, bc, kd);
-      const int r = int(i - st);
+      st = set_window_start(i, N, D, bc, kd);
+      const int r = i - st;
       const double a1 = p.c1 - p.fa * ui;
       const int kr = recentring_shift(a1, p.dt_h, D, r);
       const double c1h = fma(a1, p.dt_h, double(kr));
       lagrange_weights<D, double>(double(r - kr) + c1h, l[k]);
     }
-    ls[k] = int(st - (t0 - H));
+    ls[k] = st - (t0 - H);
     PT bound = PT(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) bound = fma(abs(l[k][j]), sT[D * NP + j], bound);
@@ -149,14 +208,21 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
 #pragma unroll
       for (int m = 0; m < D; ++m) acc[k][m] = fma(l[k][j], row[m], acc[k][m]);
   }
-  const PT e0 = p.c0dt != 0.0 ? PT(exp(p.c0dt)) : PT(1);
+  // e^{dt c0} of the identity term; a product with exactly 1 changes no bit, so it is skipped
+  const bool react = p.c0dt != 0.0;
+  const PT e0 = react ? PT(exp(p.c0dt)) : PT(1);
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     PT res = PT(0);
+    if (react) {
 #pragma unroll
-    for (int m = 0; m < D; ++m) res = fma(acc[k][m] * e0, PT(su[ls[k] + m]), res);
+      for (int m = 0; m < D; ++m) res = fma(acc[k][m] * e0, PT(su[ls[k] + m]), res);
+    } else {
+#pragma unroll
+      for (int m = 0; m < D; ++m) res = fma(acc[k][m], PT(su[ls[k] + m]), res);
+    }
     const int q = int(threadIdx.x) + k * int(blockDim.x);
-    const int64_t i = t0 + q;
+    const int i = t0 + q;
     if (vld[k] && !live[k]) out[i] = ST(i == 0 ? p.bc_lo : p.bc_hi);
     if (take[k]) {
       out[i] = res;
@@ -176,27 +242,62 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
   }
 }
 
+// Persistent: CTA c takes tiles c, c + G, c + 2G, ... (G CTAs).  While it
+// computes a tile from one shared-memory buffer, the asynchronous copies of
+// its next tile fill the other, and the tile record after that is loaded into
+// registers, so the loads of a tile overlap the arithmetic of the previous one.
 template <typename PT, int PPT>
 __global__ void __launch_bounds__(512) k_frozen_set(SetArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(16) SetInst s_in;
-  const int2 td = a.tiles[blockIdx.x];
-  const int b = td.x;
-  if (threadIdx.x < sizeof(SetInst) / 16)
-    reinterpret_cast<int4*>(&s_in)[threadIdx.x] = reinterpret_cast<const int4*>(a.inst + b)[threadIdx.x];
-  __syncthreads();
-  PT* sT = reinterpret_cast<PT*>(smem);
-  PT* su = sT + TAB_MAX;
+  __shared__ __align__(16) SetInst s_in[2];
+  const int tp = int(blockDim.x) * PPT;
+  const int stride = TAB_MAX + tp + 2 * DMAX;  // elements per buffer (a multiple of 16)
+  PT* buf = reinterpret_cast<PT*>(smem);
+  // the tile records and instance records are read-only; the state and the
+  // counters belong to the previous step's kernels
+  pdl_wait();
+  pdl_trigger();
+  const int64_t G = gridDim.x;
+  int64_t tile = blockIdx.x;
+  if (tile >= a.ntiles) return;  // the whole CTA
+  SetTile cur = a.tiles[tile];
+  stage_tile<PT>(a, cur, &s_in[0], buf, buf + TAB_MAX, tp);
+  cp_async_commit();
+  bool has_nxt = tile + G < a.ntiles;
+  SetTile nxt{};
+  if (has_nxt) nxt = a.tiles[tile + G];
   unsigned bad = 0;
-  const int64_t t0 = td.y;
-  switch (s_in.p.n) {
-    case 3: set_tile<3, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    case 5: set_tile<5, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    case 7: set_tile<7, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    case 9: set_tile<9, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    case 11: set_tile<11, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    case 13: set_tile<13, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
-    default: set_tile<15, PT, PPT>(a, s_in, b, t0, sT, su, bad); break;
+  int bi = 0;
+  for (;;) {
+    cp_async_wait_all();
+    __syncthreads();  // tile bi staged; everyone is done with buffer bi ^ 1
+    bool has_nn = false;
+    SetTile nn{};
+    if (has_nxt) {
+      PT* o = buf + (bi ^ 1) * stride;
+      stage_tile<PT>(a, nxt, &s_in[bi ^ 1], o, o + TAB_MAX, tp);
+      has_nn = tile + 2 * G < a.ntiles;
+      if (has_nn) nn = a.tiles[tile + 2 * G];
+    }
+    cp_async_commit();
+    const PT* sT = buf + bi * stride;
+    const PT* su = sT + TAB_MAX;
+    const SetInst& in = s_in[bi];
+    switch (cur.n) {
+      case 3: set_tile<3, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      case 5: set_tile<5, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      case 7: set_tile<7, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      case 9: set_tile<9, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      case 11: set_tile<11, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      case 13: set_tile<13, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+      default: set_tile<15, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+    }
+    if (!has_nxt) break;
+    cur = nxt;
+    nxt = nn;
+    has_nxt = has_nn;
+    tile += G;
+    bi ^= 1;
   }
   if (bad) atomicOr(a.flags, 1u);
 }
@@ -209,6 +310,8 @@ __global__ void __launch_bounds__(32 * WARPS) k_frozen_set_fallback(FbArgs a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Ws<PT> w(smem + warp * Ws<PT>::BYTES);
   const int64_t gw = int64_t(blockIdx.x) * WARPS + warp, nw = int64_t(gridDim.x) * WARPS;
+  pdl_wait();     // the lists and the lean kernel's outputs are complete
+  pdl_trigger();
   unsigned bad = 0;
   for (int64_t b = 0; b < a.B; ++b) {
     const int64_t cnt = a.fail_count[b];
@@ -245,6 +348,23 @@ __global__ void __launch_bounds__(32 * WARPS) k_frozen_set_fallback(FbArgs a) {
   }
 }
 
+
+// Launch with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 cudaError_t launch_set_fallback_f32(const FbArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_set_fallback_f64(const FbArgs& a, unsigned grid, cudaStream_t s);

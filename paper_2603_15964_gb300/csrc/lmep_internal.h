@@ -31,6 +31,11 @@ struct KParams {
   // a Pade scaling-and-squaring fallback (after the factorised rows, when the
   // launch carries exp(E)), 0 = Pade scaling and squaring only
   int series;
+  // constant-coefficient harvest output: weight rows stored per row class
+  // (0: 1 + n_phi) and the first of them written; rk4 = 1 stores, for
+  // n_phi = 3, the rows of exp(X), dt alpha, dt beta, dt gamma of ETDRK4
+  // (combinations of the FP64 rows of dt^k phi_k) instead of the raw rows
+  int w_rows, w_row0, rk4;
 };
 
 // Set the thread-local text returned by lmep_last_error().
@@ -77,6 +82,7 @@ struct SetLayout {
   size_t ctl, ok, inst, jobs, tiles, exps, tab, lists, total;  // byte offsets of the regions, total size
   int64_t B, ntiles, points;
   int block, ppt;
+  int grid;  // persistent grid of the lean kernel (set by frozen_set_prepare)
   bool mixed;
 };
 // Region offsets and sizes of a set of B instances (widths n[b], sizes N[b]) for
@@ -86,7 +92,7 @@ SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int b
 // width first), cleared counters, then the exp(E) tables on the device.
 // route[b] = 0: factorised rows first; 1: every point through the fallback
 // (finite series, then Pade; p.series = 0: Pade only).  Synchronises s.
-cudaError_t frozen_set_prepare(void* ws, const SetLayout& L, const KParams* p, const int32_t* route,
+cudaError_t frozen_set_prepare(void* ws, SetLayout& L, const KParams* p, const int32_t* route,
                                const int64_t* offsets, cudaStream_t s);
 // Recompute the exp(E) tables of a prepared workspace (device only).
 cudaError_t frozen_set_refresh(void* ws, const SetLayout& L, cudaStream_t s);
@@ -115,6 +121,7 @@ static_assert(sizeof(TileDesc) == 32, "TileDesc is 32 bytes");
 struct ApplyParams {
   int n, scheme, nonlin, tile;
   int halo;          // staged halo per side (apply_halo / apply_fast_halo)
+  int shift;         // window shift upstream (lmep_grid.window_shift; CTA-tiled kernel, linear scheme)
   int fast;          // 1: pipelined register-tiled kernel (periodic/Neumann, pointwise nonlinearity)
   int stages;        // fast kernel: stage slots per warp (set by apply_configure)
   int wait_polls;    // fast kernel: bound of a warp's wait for its next tile, in polls (default 2^20)
@@ -144,6 +151,22 @@ int apply_grid(const ApplyParams& a, int block, int ctas_per_sm, bool mixed);
 // Choose the fast kernel's pipeline depth for `block` threads per CTA; false
 // if the tile does not fit in shared memory.
 bool apply_configure(ApplyParams& a, bool mixed, int block);
+// ---- non-uniform grids (Sec. 4.3.3): per-node harvest (lmep_expm.cu, the warp
+// kernel's MODE_NODES; p.N, p.n, p.n_phi, the coefficients, dt, w_rows, w_row0,
+// rk4) into W[N][w_rows][n], and the apply with those stored rows
+// (lmep_apply_pw.cu; Dirichlet walls, N(u) pointwise or none).
+cudaError_t launch_harvest_nodes(const KParams& p, const double* x, void* W, bool mixed, cudaStream_t s);
+int pw_rows(int scheme);
+cudaError_t launch_apply_pw(int64_t N, int n, int scheme, int nonlin, double dt, double bc_lo, double bc_hi,
+                            const void* u, void* out, const void* W, bool mixed, unsigned* flags, cudaStream_t s);
+
+// ---- ETDRK4 apply (lmep_apply_rk4.cu): one step of one instance with the six
+// weight rows per row class of lmep_harvest_scheme_weights (E, dt alpha,
+// dt beta, dt gamma, exp(dt L / 2), (dt/2) phi_1(dt L / 2)); nonlin 1 (Allen-Cahn),
+// 2 (KdV) or 3 (Burgers).
+int rk4_halo(int n, int nonlin, int bc);
+cudaError_t launch_apply_rk4(int64_t N, double h, int bc, int n, int nonlin, double dt, double bc_lo, double bc_hi,
+                             const void* u, void* out, const void* W, bool mixed, unsigned* flags, cudaStream_t s);
 // ---- warp-streaming apply (lmep_apply_stream.cu)
 constexpr int STREAM_MAX_STAGES = 4;
 constexpr int STREAM_HEADER = 8 * STREAM_MAX_STAGES + 32 * STREAM_MAX_STAGES;  // mbarriers, tile descriptors
@@ -162,6 +185,10 @@ size_t adjoint_scratch_bytes(int64_t N, int n, bool mixed);
 cudaError_t launch_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam,
                            double* dnu, void* scratch, bool mixed, unsigned* flags, cudaStream_t s,
                            const double* sl = nullptr);
+
+// ---- Fourier symbol of a weight row (lmep_spectral.cu): G[2q], G[2q+1] = Re, Im of
+// sum_j w_j e^{i theta_q (j - r)}
+cudaError_t launch_symbol(const double* w, int n, int r, const double* theta, int64_t M, double* G, cudaStream_t s);
 
 // ---- peak (lmep_peak.cu)
 cudaError_t fma_peak(bool fp32, double* flops);

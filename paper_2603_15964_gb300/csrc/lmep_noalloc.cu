@@ -51,6 +51,8 @@ extern "C" lmep_status lmep_adjoint_step_noalloc(const lmep_grid* g, const lmep_
   if (g->n < 3 || g->n > 15 || (g->n % 2) == 0) return reject(LMEP_ERR_INVALID, "n must be odd, 3..15");
   if (g->N < g->n) return reject(LMEP_ERR_INVALID, "N must be >= n");
   if (g->batch > 1) return reject(LMEP_ERR_UNSUPPORTED, "lmep_adjoint_step_noalloc takes one instance (batch <= 1)");
+  if (g->window_shift != 0 || g->reserved != 0)
+    return reject(LMEP_ERR_UNSUPPORTED, "window_shift is for constant-coefficient linear steps");
   if (!(g->h > 0.0)) return reject(LMEP_ERR_INVALID, "h must be positive");
   if (g->bc != LMEP_BC_PERIODIC && g->bc != LMEP_BC_DIRICHLET)
     return reject(LMEP_ERR_UNSUPPORTED, "adjoint supports periodic and Dirichlet grids");

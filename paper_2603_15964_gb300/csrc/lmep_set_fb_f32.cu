@@ -9,7 +9,6 @@ cudaError_t launch_set_fallback_f32(const FbArgs& a, unsigned grid, cudaStream_t
   cudaError_t e = cudaFuncSetAttribute(k_frozen_set_fallback<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(smem));
   if (e != cudaSuccess) return e;
-  k_frozen_set_fallback<float><<<grid, 32 * WARPS, smem, s>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_frozen_set_fallback<float>, grid, 32 * WARPS, smem, s, a);
 }
 }  // namespace lmep

@@ -1,11 +1,13 @@
 // lmep_warp_kernel.cuh -- the one-warp-per-matrix kernel of steps (a1)-(a6).
 //
-// A single kernel template k_warp<D, PT> serves four jobs (runtime mode):
+// A single kernel template k_warp<D, PT> serves five jobs (runtime mode):
 //   MODE_FULL        exp(A_p) of caller matrices, whole result   (a4)
 //   MODE_CONST       constant-coefficient weight rows, one warp per
 //                    (instance, row class)                        (a1)-(a5)
 //   MODE_FROZEN_W    frozen-velocity weights of every point       (a1)-(a5)
 //   MODE_FROZEN_STEP frozen-velocity step, weights applied at once (a1)-(a6)
+//   MODE_NODES       weight rows of every node of a non-uniform grid,
+//                    one warp per node, its own derivative matrices (a1)-(a5)
 // D is the matrix dimension (n, or n + n_phi for the augmented matrix); PT
 // the Pade product type (double, or float for the FP32 form).  The state and
 // weight dtype ST equals PT.
@@ -30,7 +32,9 @@ template <typename PT>
 constexpr int dh_bytes() { return DH_BYTES + (sizeof(PT) == 4 ? DHF_BYTES : 0); }
 constexpr int WARPS = 4;                      // warps per CTA
 
-enum { MODE_FULL = 0, MODE_CONST = 1, MODE_FROZEN_W = 2, MODE_FROZEN_STEP = 3 };
+enum { MODE_FULL = 0, MODE_CONST = 1, MODE_FROZEN_W = 2, MODE_FROZEN_STEP = 3, MODE_NODES = 4 };
+// The two frozen-velocity modes (every point of a grid in chunks of 32).
+__host__ __device__ constexpr bool frozen_mode(int mode) { return mode == MODE_FROZEN_W || mode == MODE_FROZEN_STEP; }
 
 struct WarpJob {
   int mode;
@@ -40,6 +44,7 @@ struct WarpJob {
   double* E;            // MODE_FULL output
   int32_t* ms;          // MODE_FULL (m, s); frozen modes (m, s, a); nullable
   const double* h_inst; // MODE_CONST per-instance spacing, nullable
+  const double* x;      // MODE_NODES: node coordinates (device, N, strictly increasing)
   const void* u;        // frozen velocities / state
   void* out;            // weights or next state
   unsigned* flags;
@@ -364,6 +369,27 @@ __device__ __forceinline__ void frozen_chunk(const WarpJob& job, const Ws<PT>& w
   }
 }
 
+// Store the harvested rows (w.V, FP64) of a constant-coefficient or per-node
+// harvest: rows k = 0..n_phi of dt^k phi_k, or for ETDRK4 (p.rk4, n_phi = 3,
+// Sec. 3) the rows of exp(X), dt alpha, dt beta, dt gamma, formed in FP64 with
+// alpha = phi_1 - 3 phi_2 + 4 phi_3, beta = 2 phi_2 - 4 phi_3, gamma = 4 phi_3 - phi_2.
+template <typename PT>
+__device__ __forceinline__ void emit_rows(const KParams& p, const Ws<PT>& w, PT* o, int lane) {
+  const int n = p.n;
+  if (p.rk4 && p.n_phi == 3) {
+    const double i1 = 1.0 / p.dt, i2 = i1 * i1;
+    for (int j = lane; j < n; j += 32) {
+      const double w1 = w.V[DMAX + j], w2 = w.V[2 * DMAX + j] * i1, w3 = w.V[3 * DMAX + j] * i2;
+      o[j] = PT(w.V[j]);
+      o[n + j] = PT(w1 - 3.0 * w2 + 4.0 * w3);
+      o[2 * n + j] = PT(2.0 * w2 - 4.0 * w3);
+      o[3 * n + j] = PT(4.0 * w3 - w2);
+    }
+  } else {
+    for (int e = lane; e < (1 + p.n_phi) * n; e += 32) o[e] = PT(w.V[(e / n) * DMAX + e % n]);
+  }
+}
+
 template <int D, typename PT>
 __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob job) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -378,7 +404,7 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
     // factorised launches: the few rows that fall back read the tables from global memory
     Dh = const_cast<double*>(job.dh);
     if (Dhf) Dhf = const_cast<float*>(job.dhf);
-  } else if (mode != MODE_FULL) {
+  } else if (mode != MODE_FULL && mode != MODE_NODES) {
     // copy the window's derivative tables (built once per device)
     for (int e = threadIdx.x; e < 3 * DMAX * LD; e += blockDim.x) {
       Dh[e] = job.dh[e];
@@ -389,7 +415,7 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
   using ST = PT;
   ST* out = static_cast<ST*>(job.out);
   unsigned bad = 0;
-  if (mode >= MODE_FROZEN_W) {
+  if (frozen_mode(mode)) {
     static_assert(SeriesBuf<D, PT>::BYTES <= DMAX * Ws<PT>::LDM * int(sizeof(PT)) &&
                       SeriesBuf<D, double>::BYTES <= DMAX * Ws<PT>::LDM * int(sizeof(PT)),
                   "the series buffers fit in one product matrix");
@@ -417,6 +443,40 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       __syncwarp();
       continue;
     }
+    if (mode == MODE_NODES) {
+      // non-uniform grid (Sec. 4.3.3): the window's own derivative matrices, in local
+      // coordinates xi = (x - x_s) / hl (hl the window's mean spacing), built by
+      // Fornberg's recursion into the product-matrix area of the workspace, which the
+      // exponential does not use before it reads X
+      int64_t st = it - (n - 1) / 2;
+      st = st < 0 ? 0 : (st > p.N - n ? p.N - n : st);
+      const int r = int(it - st);
+      const double x0 = job.x[st];
+      const double hl = (job.x[st + n - 1] - x0) / double(n - 1);
+      static_assert(Ws<PT>::VEC_OFF - Ws<PT>::PRD_OFF >= 3 * DMAX * LD * 8,
+                    "the window's derivative tables fit between X and the harvested rows");
+      double* Dn = reinterpret_cast<double*>(w.P);
+      if (lane < n) {
+        double xs[DMAX], c[4][DMAX];
+        for (int m = 0; m < DMAX; ++m) xs[m] = m < n ? (job.x[st + m] - x0) / hl : 0.0;
+        fornberg_row_nodes(xs[lane], xs, n, c);
+        for (int k = 1; k <= 3; ++k)
+          for (int m = 0; m < DMAX; ++m) Dn[(k - 1) * DMAX * LD + lane * LD + m] = m < n ? c[k][m] : 0.0;
+      }
+      __syncwarp();
+      assemble<D>(w.X64, Dn, n, p.dt * p.c0, p.dt * p.c1 / hl, p.dt * p.c2 / (hl * hl),
+                  p.dt * p.c3 / (hl * hl * hl), lane);
+      __syncwarp();
+      augment(w.X64, n, p.n_phi, r, p.dt, lane);
+      __syncwarp();
+      int rows[4];
+      rows[0] = r;
+      for (int q = 1; q <= p.n_phi; ++q) rows[q] = n + q - 1;
+      warp_expm<D, PT>(w, lane, rows, 1 + p.n_phi, false, nullptr, 0, nullptr, nullptr);
+      emit_rows(p, w, out + it * (p.w_rows > 0 ? p.w_rows : 1 + p.n_phi) * n + int64_t(p.w_row0) * n, lane);
+      __syncwarp();
+      continue;
+    }
     if (mode == MODE_CONST) {
       int64_t b, rr;
       split_index(it, n, 2, b, rr);
@@ -441,8 +501,8 @@ __global__ void __launch_bounds__(32 * WARPS, ctas_per_sm<PT>()) k_warp(WarpJob 
       augment(w.X64, n, p.n_phi, r, p.dt, lane);
       __syncwarp();
       warp_expm<D, PT>(w, lane, rows, nrows, false, nullptr, 0, nullptr, nullptr);
-      ST* o = out + it * q1 * n;
-      for (int e = lane; e < q1 * n; e += 32) o[e] = ST(w.V[(e / n) * DMAX + e % n]);
+      const int wr = p.w_rows > 0 ? p.w_rows : q1;
+      emit_rows(p, w, out + it * wr * n + int64_t(p.w_row0) * n, lane);
       __syncwarp();
       continue;
     }
@@ -509,7 +569,7 @@ cudaError_t run_warp(const WarpJob& job_in, cudaStream_t s) {
   WarpJob job = job_in;
   int64_t need;
   need = (job.items + WARPS - 1) / WARPS;
-  if (job.mode >= MODE_FROZEN_W) {
+  if (frozen_mode(job.mode)) {
     // frozen modes: every warp of the grid (all resident) takes one contiguous
     // range of points, so that the SMs finish together
     const int64_t g = need < cap ? (need > 0 ? need : 1) : cap;

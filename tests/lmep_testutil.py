@@ -16,7 +16,7 @@ def tol(precision):
 def grid_of(p: wl.Problem):
     from paper_2603_15964_gb300 import Grid
     return Grid(N=p.N, h=p.h, bc=p.bc, n=p.n, departure_centring=p.departure_centring,
-                bc_lo=p.bc_lo, bc_hi=p.bc_hi)
+                bc_lo=p.bc_lo, bc_hi=p.bc_hi, window_shift=p.window_shift)
 
 
 def op_of(p: wl.Problem):

@@ -35,13 +35,18 @@ def test_library_exports_every_declared_symbol(lib):
 def test_host_only_calls(lib):
     assert lib.lmep_version().decode().startswith("lmep-gb300")
     assert lib.lmep_status_string(_lib.ERR_NONFINITE).decode() == "non-finite result"
-    g = _lib.LmepGrid(1000, 0.01, 0, 9, 0, 0, 0.0, 0.0)
+    g = _lib.LmepGrid(1000, 0.01, 0, 9, 0, 0, 0, 0, 0.0, 0.0)
     out = C.c_size_t()
     assert lib.lmep_adjoint_scratch_bytes(C.byref(g), 0, C.byref(out)) == _lib.OK
     assert out.value >= 1000 * 10 * 8
-    bad = _lib.LmepGrid(1000, 0.01, 0, 8, 0, 0, 0.0, 0.0)        # even stencil width
+    bad = _lib.LmepGrid(1000, 0.01, 0, 8, 0, 0, 0, 0, 0.0, 0.0)  # even stencil width
     assert lib.lmep_adjoint_scratch_bytes(C.byref(bad), 0, C.byref(out)) == _lib.ERR_INVALID
     assert "odd" in lib.lmep_last_error().decode()
+    shifted = _lib.LmepGrid(1000, 0.01, 0, 9, 0, 0, 5, 0, 0.0, 0.0)  # |window_shift| > (n-1)/2
+    assert lib.lmep_adjoint_scratch_bytes(C.byref(shifted), 0, C.byref(out)) == _lib.ERR_INVALID
+    assert "window_shift" in lib.lmep_last_error().decode()
+    reserved = _lib.LmepGrid(1000, 0.01, 0, 9, 0, 0, 0, 7, 0.0, 0.0)
+    assert lib.lmep_adjoint_scratch_bytes(C.byref(reserved), 0, C.byref(out)) == _lib.ERR_INVALID
 
 
 def test_batch_workspace_layout(lib):

@@ -559,3 +559,104 @@ def test_burgers_etd_nonlinearity_is_minus_u_ux():
     x = p.nodes()
     got = lmep.nonlinear(p, x ** 2)
     assert np.max(np.abs(got - (-(x ** 2) * 2 * x))) < 1e-12
+
+
+# ------------------------------------------------------------ high-CFL one-sided advection (Sec. 4.1)
+def _lagrange(z, n):
+    return np.array([np.prod([(z - m) / (j - m) for m in range(n) if m != j]) for j in range(n)])
+
+
+@pytest.mark.parametrize("n", [5, 9, 13])
+def test_one_sided_rows_are_departure_point_interpolation(n):
+    """Thm. 1 with a fully upwind window: the harvested row (class (n-1)/2 + k, k = (n-1)/2) is the
+    Lagrange interpolation at the departure point, r - nu in window coordinates."""
+    for sigma in (0.0, 0.3, 0.5):
+        p = wl.advection(N=64, n=n, sigma=sigma)
+        W = lmep.constant_weights(p)
+        r = (n - 1) // 2 + p.window_shift
+        want = _lagrange(r - p.meta["nu"], n)
+        assert np.max(np.abs(W[r, 0] - want)) < 1e-12 * max(1.0, np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("n", [7, 11])
+def test_one_sided_lagrangian_transport_is_exact(n):
+    """Integer Courant numbers nu = (n+1)/2: after 100 periods the profile is back exactly (the row is a
+    unit vector: a shift by nu nodes)."""
+    p = wl.advection(N=96, n=n, sigma=0.0)
+    u = lmep.run(p, wl.advection_ic(p))
+    assert np.max(np.abs(u - wl.advection_exact(p, p.steps * p.dt))) < 1e-12
+
+
+def test_one_sided_spectral_convergence_and_amplification():
+    """nu = (n+1)/2 - 1/2 (non-Lagrangian): the error after 100 periods falls by at least 5x per width
+    step, and no Fourier mode is amplified, max |G(theta)| <= 1 (up to rounding), |G(0)| = 1."""
+    errs = []
+    th = np.linspace(-np.pi, np.pi, 1001)
+    for n in (7, 9, 11, 13):
+        p = wl.advection(N=128, n=n, sigma=0.5)
+        u = lmep.run(p, wl.advection_ic(p))
+        errs.append(np.max(np.abs(u - wl.advection_exact(p, p.steps * p.dt))))
+        W = lmep.constant_weights(p)
+        r = (n - 1) // 2 + p.window_shift
+        G = np.abs(lmep.amplification(W[r, 0], r, th))
+        assert np.max(G) <= 1.0 + 1e-12 and abs(G[500] - 1.0) < 1e-13
+    assert all(errs[i + 1] < errs[i] / 5 for i in range(3)), errs
+
+
+# ------------------------------------------------------------ non-uniform (Chebyshev) grids (Sec. 4.3.3)
+from oracle import nodes as onodes  # noqa: E402
+
+
+def _cheb_matrix(x):
+    """Derivative of the polynomial interpolant at Chebyshev-Gauss-Lobatto points x_0 < ... < x_{N-1}:
+    barycentric weights w_j = (-1)^j (halved at both ends), D_ij = (w_j / w_i) / (x_i - x_j) for i != j,
+    D_ii = -sum_{j != i} D_ij (the textbook spectral differentiation matrix)."""
+    N = len(x)
+    w = np.array([(-1.0) ** j * (0.5 if j in (0, N - 1) else 1.0) for j in range(N)])
+    D = np.zeros((N, N))
+    for i in range(N):
+        for j in range(N):
+            if i != j:
+                D[i, j] = (w[j] / w[i]) / (x[i] - x[j])
+        D[i, i] = -np.sum(D[i])
+    return D
+
+
+@pytest.mark.parametrize("N", [7, 11, 15])
+def test_nodes_n_equals_N_is_the_global_chebyshev_exponential(N):
+    """One window covering a Chebyshev grid: the harvested rows are rows of the dense exp(dt L_N)
+    with L_N built from the spectral differentiation matrix (Sec. 4.3.3 avoids exactly this
+    global exponential for large N)."""
+    x = onodes.chebyshev_nodes(N)
+    p = wl.Problem("cheb", N, -1.0, 1.0, wl.DIRICHLET, N, 0.02, c1=-0.6, c2=0.01)
+    D = _cheb_matrix(x)
+    G = scipy.linalg.expm(p.dt * (p.c1 * D + p.c2 * D @ D))
+    W = onodes.weights(p, x)
+    for i in range(1, N - 1):
+        assert np.max(np.abs(W[i, 0] - G[i])) < 1e-11 * max(1.0, np.max(np.abs(G[i]))), i
+
+
+def test_nodes_uniform_grid_matches_row_classes():
+    """On uniform nodes the per-point weights are the uniform oracle's row classes."""
+    p = wl.Problem("u", 41, -1.0, 1.0, wl.DIRICHLET, 9, 0.0, c1=-0.4, c2=3e-3, scheme="etdrk2",
+                   nonlin="allen_cahn")
+    p = p.with_(dt=0.7 * p.h)
+    x = p.nodes()
+    Wn = onodes.weights(p, x)
+    Wc = lmep.constant_weights(p)
+    for i in range(1, p.N - 1):
+        idx, r = onodes.window(p, i)
+        assert np.max(np.abs(Wn[i] - Wc[r])) < 1e-12 * max(1.0, np.max(np.abs(Wc[r]))), i
+
+
+@pytest.mark.parametrize("scheme", ["linear", "etd1", "etdrk2", "etdrk4"])
+def test_nodes_constants_and_steady_states(scheme):
+    """Rows of exp(dt L) sum to 1 on any nodes (constants are annihilated by D^(k)); u = 1 with walls
+    at 1 is a steady state of Allen-Cahn (N(1) = 0) under every scheme."""
+    x = onodes.chebyshev_nodes(40)
+    p = wl.Problem("c", 40, -1.0, 1.0, wl.DIRICHLET, 9, 1e-3, c2=0.01, scheme=scheme,
+                   nonlin="none" if scheme == "linear" else "allen_cahn", bc_lo=1.0, bc_hi=1.0, steps=3)
+    W = onodes.weights(p, x)
+    assert np.max(np.abs(W[:, 0].sum(axis=1) - 1.0)) < 1e-11
+    u = onodes.run(p, x, np.ones(40))
+    assert np.max(np.abs(u - 1.0)) < 1e-11

@@ -51,6 +51,7 @@ class Problem:
     steps: int = 1
     bc_lo: float = 0.0
     bc_hi: float = 0.0
+    window_shift: int = 0       # constant coefficients: every window shifted upstream by this many nodes
     meta: dict = field(default_factory=dict, compare=False, hash=False)
 
     @property
@@ -175,6 +176,32 @@ def kdv_ic(p: Problem, seed: int = 0) -> np.ndarray:
     for k, x0 in zip(kap, xs * scale):
         u += 2.0 * k * k / np.cosh(k * (x - x0)) ** 2
     return u
+
+
+# ---------------------------------------------------------------- high-CFL advection (Sec. 4.1)
+def advection(N: int = 256, n: int = 9, sigma: float = 0.5, one_sided: bool = True, a: float = 1.0,
+              periods: float = 100.0) -> Problem:
+    """u_t + a u_x = 0, periodic on [-1, 1), IC exp(-40 x^2) (Sec. 4.1).  Courant number
+    nu = (n + 1)/2 - sigma with fully upwind (one-sided) windows, nu = 1 - sigma with centred ones;
+    dt = nu h / a; `steps` covers `periods` periods (rounded to whole steps)."""
+    p = Problem("advection", N, -1.0, 1.0, PERIODIC, n, 0.0, c1=-a, scheme="linear",
+                window_shift=(n - 1) // 2 if one_sided else 0)
+    nu = (n + 1) / 2.0 - sigma if one_sided else 1.0 - sigma
+    dt = nu * p.h / abs(a)
+    steps = int(round(periods * (p.b - p.a) / abs(a) / dt))
+    return p.with_(dt=dt, steps=steps, meta={"nu": nu, "sigma": sigma, "one_sided": one_sided})
+
+
+def advection_ic(p: Problem) -> np.ndarray:
+    return np.exp(-40.0 * p.nodes() ** 2)
+
+
+def advection_exact(p: Problem, t: float) -> np.ndarray:
+    """The initial profile carried by a t, wrapped periodically (the exact solution)."""
+    L = p.b - p.a
+    x = p.nodes()
+    xi = (x + p.c1 * t - p.a) % L + p.a          # departure point x - a t, c1 = -a
+    return np.exp(-40.0 * xi ** 2)
 
 
 # ---------------------------------------------------------------- Burgers with ETD (Sec. 4.3.1)
