@@ -789,6 +789,80 @@ def adjoint_main(args, rank, world, local_rank, cores):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_full_main(args, rank, world, local_rank, cores):
+    """Configuration 5 at its stated size: 256 initial states x N = 262144, 2048 steps, a checkpoint every
+    64 steps; one gradient of J = h/2 sum_b ||u_b(T) - u*_b||^2 with respect to the initial states and nu
+    through torch.autograd (FP32 forward, FP64 derivatives), timed with CUDA events and with the clocks
+    sampled; then central differences of the GPU forward: along a seeded direction v in the initial states,
+    (J(x0 + e v) - J(x0 - e v)) / 2e against <dJ/dx0, v>, and in nu."""
+    import numpy as np
+    import torch
+
+    import paper_2603_15964_gb300 as L
+    import workloads as wl
+    from paper_2603_15964_gb300.autograd import FrozenVelocitySolver
+    if rank != 0:
+        return
+    B, K, C = max(1, args.adj_batch), max(1, args.adj_steps), max(1, args.adj_checkpoint)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    p = adj_problem(K)
+    x0 = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, q) for q in range(B)]).astype(np.float32), device=dev)
+    tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + q) for q in range(B)]).astype(np.float32), device=dev)
+    solver = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="mixed", checkpoint_every=C)
+
+    def J_of(x, nu_v):
+        with torch.no_grad():
+            uT = solver(x, torch.tensor(nu_v, dtype=torch.float64))
+            return 0.5 * p.h * float(((uT.double() - tgt.double()) ** 2).sum())
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    x = x0.clone().requires_grad_(True)
+    nu = torch.tensor(p.c2, dtype=torch.float64, requires_grad=True)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    uT = solver(x, nu)
+    Jt = 0.5 * p.h * ((uT.double() - tgt.double()) ** 2).sum()
+    e1.record()
+    Jt.backward()
+    e2.record()
+    e2.synchronize()
+    clk = clocks.stop()
+    L.lmep_sync_status(solver.handle)
+    fwd_ms, rev_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    g = x.grad.double()
+    gnu = float(nu.grad)
+    v = torch.tensor(np.random.default_rng(7).standard_normal((B, ADJ_N)), dtype=torch.float64, device=dev)
+    v[:, 0] = 0.0
+    v[:, -1] = 0.0
+    eps = 1e-3
+    t0 = time.perf_counter()
+    jp = J_of((x0.double() + eps * v).float(), p.c2)
+    jm = J_of((x0.double() - eps * v).float(), p.c2)
+    dv_fd = (jp - jm) / (2 * eps)
+    dv_ad = float((g * v).sum())
+    en = 0.25 * p.c2
+    dnu_fd = (J_of(x0, p.c2 + en) - J_of(x0, p.c2 - en)) / (2 * en)
+    fd_s = time.perf_counter() - t0
+    total = fwd_ms + rev_ms
+    line = {"metric": "gradient point-steps/s (forward + reverse)", "value": ADJ_N * B * K / (total * 1e-3),
+            "unit": "point-steps/s", "n_gpus": 1, "steps": K, "warmup": 0, "ms_per_step": total / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 forward + f64 derivatives", "data": "synthetic",
+            "config": {"workload": f"configuration 5 at full size: {B} x N = {ADJ_N}, {K} steps, checkpoint every "
+                                   f"{C}, n = {ADJ_NS}, CFL {ADJ_CFL}, nu = {NU}, J = h/2 sum ||u(T) - u*||^2"},
+            "forward_ms": fwd_ms, "reverse_ms": rev_ms, "clocks": clk,
+            "check": {"directional_u0": {"adjoint": dv_ad, "central_difference": dv_fd, "eps": eps,
+                                         "rel_diff": abs(dv_ad - dv_fd) / max(abs(dv_fd), 1e-300)},
+                      "nu": {"adjoint": gnu, "central_difference": dnu_fd, "eps": en,
+                             "rel_diff": abs(gnu - dnu_fd) / max(abs(dnu_fd), 1e-300)},
+                      "what": "central differences of the GPU forward (FP32 state, J in FP64)",
+                      "seconds": fd_s},
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ stand-alone apply sweep (a6)
 def _oracle_apply(task):
     """Oracle steps of a periodic instance: time per point-update on a bounded size."""
@@ -1358,14 +1432,17 @@ def main():
                     help="oracle points per instance for cpu_baseline (0: every interior point of the step)")
     ap.add_argument("--cpu-points", type=float, default=12e6,
                     help="Allen-Cahn cpu_baseline: oracle point-updates (whole instances in batch order)")
-    ap.add_argument("--workload", choices=["burgers", "allen_cahn", "adjoint", "apply_sweep"], default="burgers",
+    ap.add_argument("--workload", choices=["burgers", "allen_cahn", "adjoint", "adjoint_full", "apply_sweep"],
+                    default="burgers",
                     help="burgers: the frozen-velocity step (default); allen_cahn: the batched ETDRK2 apply; "
                          "adjoint: forward + reverse sweep of the frozen-velocity step (gradient); "
+                         "adjoint_full: configuration 5 at its stated size with central-difference checks; "
                          "apply_sweep: the stored-weight apply on one large instance (HBM roofline)")
     ap.add_argument("--sweep-log2n", type=int, default=26, help="apply_sweep: log2 of the instance size")
     ap.add_argument("--instances", type=int, default=4096, help="Allen-Cahn batch size")
     ap.add_argument("--adj-batch", type=int, default=8, help="adjoint workload: Burgers instances per launch")
     ap.add_argument("--adj-steps", type=int, default=4, help="adjoint workload: forward + reverse steps timed")
+    ap.add_argument("--adj-checkpoint", type=int, default=64, help="adjoint_full: steps between checkpoints")
     ap.add_argument("--headline-only", action="store_true",
                     help="Burgers workload: skip the other configurations' legs (`configs` key)")
     ap.add_argument("--profile-case", nargs="+", default=None,
@@ -1385,6 +1462,8 @@ def main():
         return allen_cahn_main(args, rank, world, local_rank, cores)
     if args.workload == "adjoint":
         return adjoint_main(args, rank, world, local_rank, cores)
+    if args.workload == "adjoint_full":
+        return adjoint_full_main(args, rank, world, local_rank, cores)
     if args.workload == "apply_sweep":
         return apply_sweep_main(args, rank, world, local_rank, cores)
 
