@@ -793,8 +793,9 @@ def adjoint_full_main(args, rank, world, local_rank, cores):
     """Configuration 5 at its stated size: 256 initial states x N = 262144, 2048 steps, a checkpoint every
     64 steps; one gradient of J = h/2 sum_b ||u_b(T) - u*_b||^2 with respect to the initial states and nu
     through torch.autograd (FP32 forward, FP64 derivatives), timed with CUDA events and with the clocks
-    sampled; then central differences of the GPU forward: along a seeded direction v in the initial states,
-    (J(x0 + e v) - J(x0 - e v)) / 2e against <dJ/dx0, v>, and in nu."""
+    sampled; then, on the first four instances, central differences of the FP64 GPU forward along a seeded
+    direction v in the initial states, (J(x0 + e v) - J(x0 - e v)) / 2e, against <dJ/dx0, v> of the timed
+    run and of the FP64 adjoint, and the same in nu."""
     import numpy as np
     import torch
 
@@ -810,11 +811,6 @@ def adjoint_full_main(args, rank, world, local_rank, cores):
     x0 = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, q) for q in range(B)]).astype(np.float32), device=dev)
     tgt = torch.tensor(np.stack([wl.burgers_ic(ADJ_N, 1000 + q) for q in range(B)]).astype(np.float32), device=dev)
     solver = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="mixed", checkpoint_every=C)
-
-    def J_of(x, nu_v):
-        with torch.no_grad():
-            uT = solver(x, torch.tensor(nu_v, dtype=torch.float64))
-            return 0.5 * p.h * float(((uT.double() - tgt.double()) ** 2).sum())
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -833,17 +829,41 @@ def adjoint_full_main(args, rank, world, local_rank, cores):
     fwd_ms, rev_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     g = x.grad.double()
     gnu = float(nu.grad)
-    v = torch.tensor(np.random.default_rng(7).standard_normal((B, ADJ_N)), dtype=torch.float64, device=dev)
+    # checks on a subset S of the instances (J is a sum over instances, so the gradient in x_b is that of
+    # J_S for b in S): the full run's gradient on S and the FP64 adjoint on S against central differences
+    # of the FP64 forward on S (FP32 rounding of the state would swamp differences of this size)
+    S = min(4, B)
+    t0 = time.perf_counter()
+    s64 = FrozenVelocitySolver(N=ADJ_N, h=p.h, n=p.n, dt=p.dt, steps=K, precision="fp64", checkpoint_every=C)
+    tgt_s = tgt[:S].double()
+
+    def J_sub(solver_, x, nu_v, grad=False):
+        nu_t = torch.tensor(nu_v, dtype=torch.float64, requires_grad=grad)
+        if grad:
+            x = x.clone().requires_grad_(True)
+            uT_ = solver_(x, nu_t)
+            J_ = 0.5 * p.h * ((uT_.double() - tgt_s) ** 2).sum()
+            J_.backward()
+            return float(J_.detach()), x.grad.double(), float(nu_t.grad)
+        with torch.no_grad():
+            uT_ = solver_(x, nu_t)
+            return 0.5 * p.h * float(((uT_.double() - tgt_s) ** 2).sum()), None, None
+
+    x0s = x0[:S].double()
+    _, g64, gnu64 = J_sub(s64, x0s, p.c2, grad=True)
+    _, _, gnu_mixed_s = J_sub(solver, x0[:S], p.c2, grad=True)
+    v = torch.tensor(np.random.default_rng(7).standard_normal((S, ADJ_N)), dtype=torch.float64, device=dev)
     v[:, 0] = 0.0
     v[:, -1] = 0.0
-    eps = 1e-3
-    t0 = time.perf_counter()
-    jp = J_of((x0.double() + eps * v).float(), p.c2)
-    jm = J_of((x0.double() - eps * v).float(), p.c2)
-    dv_fd = (jp - jm) / (2 * eps)
-    dv_ad = float((g * v).sum())
-    en = 0.25 * p.c2
-    dnu_fd = (J_of(x0, p.c2 + en) - J_of(x0, p.c2 - en)) / (2 * en)
+    # two step sizes: the central difference's O(eps^2) truncation shows as a 100-fold drop of the gap
+    fd = {}
+    for eps in (1e-3, 1e-4):
+        fd[eps] = (J_sub(s64, x0s + eps * v, p.c2)[0] - J_sub(s64, x0s - eps * v, p.c2)[0]) / (2 * eps)
+    dv_fd = fd[1e-4]
+    dv_ad = float((g[:S] * v).sum())
+    dv_64 = float((g64 * v).sum())
+    en = 0.01 * p.c2
+    dnu_fd = (J_sub(s64, x0s, p.c2 + en)[0] - J_sub(s64, x0s, p.c2 - en)[0]) / (2 * en)
     fd_s = time.perf_counter() - t0
     total = fwd_ms + rev_ms
     line = {"metric": "gradient point-steps/s (forward + reverse)", "value": ADJ_N * B * K / (total * 1e-3),
@@ -853,11 +873,19 @@ def adjoint_full_main(args, rank, world, local_rank, cores):
             "config": {"workload": f"configuration 5 at full size: {B} x N = {ADJ_N}, {K} steps, checkpoint every "
                                    f"{C}, n = {ADJ_NS}, CFL {ADJ_CFL}, nu = {NU}, J = h/2 sum ||u(T) - u*||^2"},
             "forward_ms": fwd_ms, "reverse_ms": rev_ms, "clocks": clk,
-            "check": {"directional_u0": {"adjoint": dv_ad, "central_difference": dv_fd, "eps": eps,
-                                         "rel_diff": abs(dv_ad - dv_fd) / max(abs(dv_fd), 1e-300)},
-                      "nu": {"adjoint": gnu, "central_difference": dnu_fd, "eps": en,
-                             "rel_diff": abs(gnu - dnu_fd) / max(abs(dnu_fd), 1e-300)},
-                      "what": "central differences of the GPU forward (FP32 state, J in FP64)",
+            "dJ_dnu": gnu,
+            "check": {"instances": S,
+                      "directional_u0": {"adjoint_full_run": dv_ad, "adjoint_fp64": dv_64,
+                                         "central_difference_fp64": dv_fd, "eps": 1e-4,
+                                         "central_difference_fp64_eps_1e-3": fd[1e-3],
+                                         "rel_diff_full_run": abs(dv_ad - dv_fd) / max(abs(dv_fd), 1e-300),
+                                         "rel_diff_fp64": abs(dv_64 - dv_fd) / max(abs(dv_fd), 1e-300)},
+                      "nu": {"adjoint_mixed": gnu_mixed_s, "adjoint_fp64": gnu64,
+                             "central_difference_fp64": dnu_fd, "eps": en,
+                             "rel_diff_mixed": abs(gnu_mixed_s - dnu_fd) / max(abs(dnu_fd), 1e-300),
+                             "rel_diff_fp64": abs(gnu64 - dnu_fd) / max(abs(dnu_fd), 1e-300)},
+                      "what": "on the first instances: the full run's gradient and the FP64 adjoint against "
+                              "central differences of the FP64 GPU forward (J in FP64)",
                       "seconds": fd_s},
             "gpu_launches": None}
     print(json.dumps(line), flush=True)

@@ -266,9 +266,10 @@ LMEP_API lmep_status lmep_frozen_set_prepare(lmep_handle* h, const lmep_frozen_s
  * launch, no host memory touched; the per-run setup cost of the set). */
 LMEP_API lmep_status lmep_frozen_set_refresh(lmep_handle* h, void* workspace_dev, void* stream);
 /* One step of every instance from u_in_dev to u_out_dev (distinct,
- * non-overlapping buffers): two launches, no host synchronisation, suitable
- * for replay in a CUDA graph that alternates the two buffers.  Calls that
- * share a workspace must not overlap on the GPU. */
+ * non-overlapping buffers): two launches (the lean kernel, then the fallback
+ * for the points it rejected, which returns at once when there are none), no
+ * host synchronisation, suitable for replay in a CUDA graph that alternates
+ * the two buffers.  Calls that share a workspace must not overlap on the GPU. */
 LMEP_API lmep_status lmep_frozen_set_step_once(lmep_handle* h, const void* workspace_dev, const void* u_in_dev,
                                                void* u_out_dev, void* stream);
 

@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "lmep_frozen_set.cuh"
@@ -137,11 +139,12 @@ SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int b
   L.ppt = ppt;
   L.mixed = mixed;
   L.ctl = 0;
-  L.ok = align256(L.ctl + size_t(B + 1) * 4);
+  L.ok = align256(L.ctl + size_t(B + 2) * 4);  // counts, done, total
   L.inst = align256(L.ok + size_t(B) * 4);
   L.jobs = align256(L.inst + size_t(B) * sizeof(SetInst));
   L.tiles = align256(L.jobs + size_t(B) * sizeof(WarpJob));
-  L.exps = align256(L.tiles + size_t(tiles) * sizeof(SetTile));
+  L.starts = align256(L.tiles + size_t(tiles) * sizeof(SetTile));
+  L.exps = align256(L.starts + size_t(tiles + 1) * 4);  // the grid never exceeds the tile count
   L.tab = align256(L.exps + size_t(B) * 2 * DMAX * DMAX * 8);
   L.lists = align256(L.tab + size_t(tabn) * es);
   L.total = align256(L.lists + size_t(points) * 4);
@@ -177,24 +180,52 @@ cudaError_t frozen_set_prepare(void* ws, SetLayout& L, const KParams* p, const i
     cudaError_t e = fornberg_of(p[b].n, &j.dh, &j.dhf);
     if (e != cudaSuccess) return e;
   }
-  // tiles of the widest stencils first: the costliest CTAs start in the first wave
-  std::vector<int64_t> order(size_t(L.B));
-  for (int64_t b = 0; b < L.B; ++b) order[size_t(b)] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return p[x].n > p[y].n; });
-  for (int64_t b : order)
-    for (int64_t t0 = 0; t0 < p[b].N; t0 += tp) {
+  // Tiles to CTAs, longest processing time first: tiles in decreasing estimated
+  // cost (points x (n^2 + 8n + 40), the row product, weights, bound and apply),
+  // each to the CTA with the least work so far; a CTA's tiles are stored
+  // together, heaviest first, from starts[c] to starts[c + 1].
+  struct Job {
+    double cost;
+    int64_t b, t0;
+  };
+  std::vector<Job> work;
+  work.reserve(size_t(L.ntiles));
+  for (int64_t b = 0; b < L.B; ++b) {
+    const double w = double(p[b].n) * p[b].n + 8.0 * p[b].n + 40.0;
+    for (int64_t t0 = 0; t0 < p[b].N; t0 += tp) work.push_back({w * double(std::min(tp, p[b].N - t0)), b, t0});
+  }
+  std::stable_sort(work.begin(), work.end(), [](const Job& x, const Job& y) { return x.cost > y.cost; });
+  const int G = L.grid;
+  std::vector<std::vector<int64_t>> runs(static_cast<size_t>(G));
+  using Load = std::pair<double, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int c = 0; c < G; ++c) heap.push({0.0, c});
+  for (size_t q = 0; q < work.size(); ++q) {
+    Load top = heap.top();
+    heap.pop();
+    runs[size_t(top.second)].push_back(int64_t(q));
+    top.first += work[q].cost;
+    heap.push(top);
+  }
+  std::vector<int32_t> starts(size_t(G) + 1, 0);
+  for (int c = 0; c < G; ++c) {
+    starts[size_t(c)] = int32_t(tiles.size());
+    for (int64_t q : runs[size_t(c)]) {
+      const Job& j = work[size_t(q)];
       SetTile t{};
-      t.off = inst[size_t(b)].off;
-      t.N = int32_t(p[b].N);
-      t.t0 = int32_t(t0);
-      t.b = int32_t(b);
-      t.n = p[b].n;
-      t.bc = p[b].bc;
-      t.tab = int32_t(inst[size_t(b)].tab);
+      t.off = inst[size_t(j.b)].off;
+      t.N = int32_t(p[j.b].N);
+      t.t0 = int32_t(j.t0);
+      t.b = int32_t(j.b);
+      t.n = p[j.b].n;
+      t.bc = p[j.b].bc;
+      t.tab = int32_t(inst[size_t(j.b)].tab);
       tiles.push_back(t);
     }
+  }
+  starts[size_t(G)] = int32_t(tiles.size());
   cudaError_t e;
-  if ((e = cudaMemsetAsync(base + L.ctl, 0, size_t(L.B + 1) * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(base + L.ctl, 0, size_t(L.B + 2) * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(base + L.inst, inst.data(), inst.size() * sizeof(SetInst), cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
@@ -202,6 +233,9 @@ cudaError_t frozen_set_prepare(void* ws, SetLayout& L, const KParams* p, const i
       cudaSuccess)
     return e;
   if ((e = cudaMemcpyAsync(base + L.tiles, tiles.data(), tiles.size() * sizeof(SetTile), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(base + L.starts, starts.data(), starts.size() * 4, cudaMemcpyHostToDevice, s)) !=
       cudaSuccess)
     return e;
   if ((e = frozen_set_refresh(ws, L, s)) != cudaSuccess) return e;
@@ -234,10 +268,11 @@ cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_o
   SetArgs a;
   a.inst = reinterpret_cast<const SetInst*>(base + L.inst);
   a.tiles = reinterpret_cast<const SetTile*>(base + L.tiles);
-  a.ntiles = L.ntiles;
+  a.starts = reinterpret_cast<const int32_t*>(base + L.starts);
   a.tab = base + L.tab;
   a.ok = reinterpret_cast<const int32_t*>(base + L.ok);
   a.fail_count = reinterpret_cast<int32_t*>(base + L.ctl);
+  a.fail_total = a.fail_count + L.B + 1;
   a.fail_list = reinterpret_cast<int32_t*>(base + L.lists);
   a.u = u_in;
   a.out = u_out;
@@ -250,6 +285,7 @@ cudaError_t set_step(char* base, const SetLayout& L, const void* u_in, void* u_o
   f.inst = a.inst;
   f.jobs = reinterpret_cast<const WarpJob*>(base + L.jobs);
   f.fail_count = a.fail_count;
+  f.fail_total = a.fail_total;
   f.fail_list = a.fail_list;
   f.done = reinterpret_cast<unsigned*>(base + L.ctl) + L.B;
   f.B = L.B;

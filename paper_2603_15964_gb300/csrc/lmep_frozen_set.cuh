@@ -4,6 +4,7 @@
 // units (lmep_set_fb_f32.cu, lmep_set_fb_f64.cu).
 #pragma once
 
+#include "lmep_stream.cuh"
 #include "lmep_warp_kernel.cuh"
 
 namespace lmep {
@@ -34,11 +35,12 @@ static_assert(sizeof(SetTile) == 32, "SetTile is 32 bytes");
 
 struct SetArgs {
   const SetInst* inst;
-  const SetTile* tiles;
-  int64_t ntiles;
+  const SetTile* tiles;   // CTA c's tiles are tiles[starts[c] .. starts[c + 1])
+  const int32_t* starts;  // (the API caps a set at 2^31 - 1 tiles)
   const void* tab;
   const int32_t* ok;  // per instance: 1 when its exp(E) table is finite
   int32_t* fail_count;
+  int32_t* fail_total;  // rejected points of all instances (the fallback's early exit)
   int32_t* fail_list;
   const void* u;
   void* out;
@@ -49,6 +51,7 @@ struct FbArgs {
   const SetInst* inst;
   const WarpJob* jobs;
   int32_t* fail_count;
+  int32_t* fail_total;
   const int32_t* fail_list;
   unsigned* done;
   int64_t B;
@@ -193,20 +196,53 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
     for (int j = 0; j < D; ++j) bound = fma(abs(l[k][j]), sT[D * NP + j], bound);
     take[k] = live[k] && fact && bound <= PT(SL_TAU);
   }
-  // row_m = sum_j l_j exp(E)[j][m]: row j of the table is read once for all PPT points
+  // row_m = sum_j l_j exp(E)[j][m]: row j of the table is read once for all PPT points.
+  // FP32: columns m, m + 1 in one packed f32x2 FMA (each lane an IEEE fma, so
+  // the bits are those of the scalar sums); an odd width's last pair carries
+  // the table's zero padding in its upper lane, which is never read.
   PT acc[PPT][D];
-#pragma unroll
-  for (int k = 0; k < PPT; ++k)
-#pragma unroll
-    for (int m = 0; m < D; ++m) acc[k][m] = PT(0);
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    PT row[NP];
-    load_row<PT, NP>(sT + j * NP, row);
+  if constexpr (F32) {
+    using PO = PairOps<float>;
+    constexpr int DP = (D + 1) / 2;
+    PO::T acc2[PPT][DP];
 #pragma unroll
     for (int k = 0; k < PPT; ++k)
 #pragma unroll
-      for (int m = 0; m < D; ++m) acc[k][m] = fma(l[k][j], row[m], acc[k][m]);
+      for (int m = 0; m < DP; ++m) acc2[k][m] = 0ull;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      PO::T row[NP / 2];
+      PO::template load<NP / 2>(sT + j * NP, row);
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const PO::T lj = PO::make(l[k][j], l[k][j]);
+#pragma unroll
+        for (int m = 0; m < DP; ++m) acc2[k][m] = PO::fma(lj, row[m], acc2[k][m]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+#pragma unroll
+      for (int m = 0; m < DP; ++m) {
+        float lo, hi;
+        PO::split(acc2[k][m], lo, hi);
+        acc[k][2 * m] = lo;
+        if (2 * m + 1 < D) acc[k][2 * m + 1] = hi;
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+#pragma unroll
+      for (int m = 0; m < D; ++m) acc[k][m] = PT(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      PT row[NP];
+      load_row<PT, NP>(sT + j * NP, row);
+#pragma unroll
+      for (int k = 0; k < PPT; ++k)
+#pragma unroll
+        for (int m = 0; m < D; ++m) acc[k][m] = fma(l[k][j], row[m], acc[k][m]);
+    }
   }
   // e^{dt c0} of the identity term; a product with exactly 1 changes no bit, so it is skipped
   const bool react = p.c0dt != 0.0;
@@ -235,38 +271,26 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
       const int lane = threadIdx.x & 31;
       const int lead = __ffs(m) - 1;
       int base = 0;
-      if (lane == lead) base = atomicAdd(a.fail_count + b, __popc(m));
+      if (lane == lead) {
+        base = atomicAdd(a.fail_count + b, __popc(m));
+        atomicAdd(a.fail_total, __popc(m));
+      }
       base = __shfl_sync(FULL, base, lead);
       if (rej) a.fail_list[in.list_off + base + __popc(m & ((1u << lane) - 1u))] = int32_t(i);
     }
   }
 }
 
-// Persistent: CTA c takes tiles c, c + G, c + 2G, ... (G CTAs).  While it
-// computes a tile from one shared-memory buffer, the asynchronous copies of
-// its next tile fill the other, and the tile record after that is loaded into
-// registers, so the loads of a tile overlap the arithmetic of the previous one.
+// The tiles tile .. end - 1 of a CTA, staged two buffers deep.
 template <typename PT, int PPT>
-__global__ void __launch_bounds__(512) k_frozen_set(SetArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ __align__(16) SetInst s_in[2];
-  const int tp = int(blockDim.x) * PPT;
-  const int stride = TAB_MAX + tp + 2 * DMAX;  // elements per buffer (a multiple of 16)
-  PT* buf = reinterpret_cast<PT*>(smem);
-  // the tile records and instance records are read-only; the state and the
-  // counters belong to the previous step's kernels
-  pdl_wait();
-  pdl_trigger();
-  const int64_t G = gridDim.x;
-  int64_t tile = blockIdx.x;
-  if (tile >= a.ntiles) return;  // the whole CTA
+__device__ __forceinline__ void set_tiles(const SetArgs& a, int tile, const int end, PT* buf, SetInst* s_in,
+                                          const int stride, const int tp, unsigned& bad) {
   SetTile cur = a.tiles[tile];
   stage_tile<PT>(a, cur, &s_in[0], buf, buf + TAB_MAX, tp);
   cp_async_commit();
-  bool has_nxt = tile + G < a.ntiles;
+  bool has_nxt = tile + 1 < end;
   SetTile nxt{};
-  if (has_nxt) nxt = a.tiles[tile + G];
-  unsigned bad = 0;
+  if (has_nxt) nxt = a.tiles[tile + 1];
   int bi = 0;
   for (;;) {
     cp_async_wait_all();
@@ -276,8 +300,8 @@ __global__ void __launch_bounds__(512) k_frozen_set(SetArgs a) {
     if (has_nxt) {
       PT* o = buf + (bi ^ 1) * stride;
       stage_tile<PT>(a, nxt, &s_in[bi ^ 1], o, o + TAB_MAX, tp);
-      has_nn = tile + 2 * G < a.ntiles;
-      if (has_nn) nn = a.tiles[tile + 2 * G];
+      has_nn = tile + 2 < end;
+      if (has_nn) nn = a.tiles[tile + 2];
     }
     cp_async_commit();
     const PT* sT = buf + bi * stride;
@@ -296,9 +320,32 @@ __global__ void __launch_bounds__(512) k_frozen_set(SetArgs a) {
     cur = nxt;
     nxt = nn;
     has_nxt = has_nn;
-    tile += G;
+    ++tile;
     bi ^= 1;
   }
+}
+
+// Persistent: CTA c takes its own run of tiles (balanced on the host).  While
+// it computes a tile from one shared-memory buffer, the asynchronous copies of
+// its next tile fill the other, and the tile record after that is loaded into
+// registers, so the loads of a tile overlap the arithmetic of the previous one.
+// One point per thread: at most 64 registers, so that 8 CTAs of 128 threads
+// (or 2 of 512) fit on an SM.
+template <typename PT, int PPT>
+__global__ void __launch_bounds__(512, PPT == 1 ? 2 : 1) k_frozen_set(SetArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) SetInst s_in[2];
+  const int tp = int(blockDim.x) * PPT;
+  const int stride = TAB_MAX + tp + 2 * DMAX;  // elements per buffer (a multiple of 16)
+  PT* buf = reinterpret_cast<PT*>(smem);
+  // the tile records and instance records are read-only; the state and the
+  // counters belong to the previous step's kernels
+  pdl_wait();
+  pdl_trigger();
+  int tile = a.starts[blockIdx.x];
+  const int end = a.starts[blockIdx.x + 1];
+  unsigned bad = 0;
+  if (tile < end) set_tiles<PT, PPT>(a, tile, end, buf, s_in, stride, tp, bad);
   if (bad) atomicOr(a.flags, 1u);
 }
 
@@ -312,6 +359,10 @@ __global__ void __launch_bounds__(32 * WARPS) k_frozen_set_fallback(FbArgs a) {
   const int64_t gw = int64_t(blockIdx.x) * WARPS + warp, nw = int64_t(gridDim.x) * WARPS;
   pdl_wait();     // the lists and the lean kernel's outputs are complete
   pdl_trigger();
+  // nothing rejected (the usual case): every CTA leaves after one load, and
+  // the counters are all zero already.  The total is cleared only by the last
+  // CTA below, after every CTA has read it, so all CTAs take the same branch.
+  if (*static_cast<volatile const int32_t*>(a.fail_total) == 0) return;
   unsigned bad = 0;
   for (int64_t b = 0; b < a.B; ++b) {
     const int64_t cnt = a.fail_count[b];
@@ -342,6 +393,7 @@ __global__ void __launch_bounds__(32 * WARPS) k_frozen_set_fallback(FbArgs a) {
     __threadfence();
     if (atomicAdd(a.done, 1u) == gridDim.x - 1) {
       for (int64_t b = 0; b < a.B; ++b) a.fail_count[b] = 0;
+      *a.fail_total = 0;
       *a.done = 0;
       __threadfence();
     }

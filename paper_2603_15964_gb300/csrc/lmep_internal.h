@@ -79,7 +79,7 @@ cudaError_t launch_exp_const(const KParams& p, double* out, double* out2, cudaSt
 // its own grid, operator, dt and stencil width, advanced by one launch per
 // step (plus a launch that finishes the rare points the first one rejects).
 struct SetLayout {
-  size_t ctl, ok, inst, jobs, tiles, exps, tab, lists, total;  // byte offsets of the regions, total size
+  size_t ctl, ok, inst, jobs, tiles, starts, exps, tab, lists, total;  // byte offsets of the regions, total size
   int64_t B, ntiles, points;
   int block, ppt;
   int grid;  // persistent grid of the lean kernel (set by frozen_set_prepare)
@@ -88,8 +88,9 @@ struct SetLayout {
 // Region offsets and sizes of a set of B instances (widths n[b], sizes N[b]) for
 // tiles of block * ppt points.
 SetLayout frozen_set_layout(int64_t B, const int32_t* n, const int64_t* N, int block, int ppt, bool mixed);
-// Fill a workspace: instance records, fallback jobs, tile table (heaviest
-// width first), cleared counters, then the exp(E) tables on the device.
+// Fill a workspace: instance records, fallback jobs, tile table (each CTA's
+// tiles together, balanced by estimated cost), cleared counters, then the
+// exp(E) tables on the device.
 // route[b] = 0: factorised rows first; 1: every point through the fallback
 // (finite series, then Pade; p.series = 0: Pade only).  Synchronises s.
 cudaError_t frozen_set_prepare(void* ws, SetLayout& L, const KParams* p, const int32_t* route,

@@ -155,6 +155,27 @@ def test_set_graph_replay_matches_eager(L, precision):
         assert same_bits(a, b)
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_set_graph_replay_without_rejections(L, precision):
+    # nu = 1e-6: every point takes the factorised row, so every fallback launch leaves at once; the
+    # replayed states equal eager steps bit for bit and the counters (per-instance counts, the fallback's
+    # arrival counter, the total) stay clear
+    probs = [wl.burgers(N=5000, n=13, cfl=4.0, nu=1e-6, seed=11), wl.burgers(N=3333, n=7, cfl=1.0, nu=1e-6, seed=12)]
+    u0 = [ic_of(p, s) for s, p in enumerate(probs)]
+    eager = make_set(L, probs, precision)
+    eager.load(u0)
+    eager.step(6)
+    graph = make_set(L, probs, precision)
+    graph.load(u0)
+    graph.capture()
+    graph.replay(4)
+    torch.cuda.synchronize()
+    for a, b in zip(eager.states, graph.states):
+        assert same_bits(a, b)
+    ctl = graph.workspace[:4 * (len(probs) + 2)].view(torch.int32).cpu().tolist()
+    assert ctl == [0] * (len(probs) + 2), ctl
+
+
 def test_set_refresh_is_idempotent(L):
     """Recomputing the exp(E) tables on the device gives the same steps."""
     probs = mixed_probs()[:3]
