@@ -1241,7 +1241,16 @@ def cfg_etdrk4(L, h, K: int = 20):
         L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, work, 2, prec)
         ms = _timed_ms(lambda: L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, work, K, prec)) / K
         gbs = 2.0 * es * p.N / (ms * 1e-3) / 1e9
-        out[prec] = {"point_updates_per_s": p.N / (ms * 1e-3), "ms_per_step": ms, "GB_s": gbs, "frac": gbs / peak}
+        # ALU roofline: per point four N(.) with a derivative stencil (2n + 2), three half stages of two
+        # stencils (4n), the combination (3) and the final four stencils (8n): 28 n + 11 FLOPs
+        flops = 28 * p.n + 11
+        tf = flops * p.N / (ms * 1e-3) / 1e12
+        pk = (P32_NOMINAL if prec == "mixed" else P64_NOMINAL) / 1e12
+        out[prec] = {"point_updates_per_s": p.N / (ms * 1e-3), "ms_per_step": ms, "GB_s": gbs, "frac": gbs / peak,
+                     "roofline": {"bound": "alu", "flops_per_point": flops, "achieved": tf, "peak": pk,
+                                  "unit": "TFLOP/s", "frac": tf / pk,
+                                  "peak_source": "nominal " + ("FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz)"
+                                                               if prec == "mixed" else "FP64 (GB300)")}}
     L.lmep_sync_status(h)
     return out
 

@@ -48,7 +48,23 @@ def cases():
                                  .with_(bc=wl.DIRICHLET, a=-1.0, b=1.0), None),
         "ac_reaction_c0_n5": (wl.Problem("r", 777, 0.0, 1.0, wl.PERIODIC, 5, 0.02, c0=-1.5, c2=2e-6,
                                          scheme="etdrk4", nonlin="allen_cahn", steps=5), 4),
+        # walled grids of several tiles (2048 points in FP32, 1024 in FP64): the tiles whose halo stays
+        # clear of the walls take the interior path, the two next to the walls the per-point path
+        "ac_dirichlet_tiles_n9": (wl.allen_cahn(9001, bc=wl.DIRICHLET, n=9, scheme="etdrk4", steps=3, mu=0.5)
+                                  .with_(bc_lo=-1.0, bc_hi=1.0), 5),
+        "burgers_dirichlet_tiles_n9": (wl.burgers_etd(N=7001, n=9, nu=1e-3, dt=4e-5, steps=3)
+                                       .with_(bc=wl.DIRICHLET, a=-1.0, b=1.0), None),
+        "burgers_dirichlet_tiles_n13": (wl.burgers_etd(N=7001, n=13, nu=1e-3, dt=1.5e-4, steps=3)
+                                        .with_(bc=wl.DIRICHLET, a=-1.0, b=1.0), None),
     }
+
+
+def wall_kappa(p):
+    """Largest l1 norm of an updated row of exp(dt L) (1 on periodic and Neumann grids)."""
+    if p.bc != wl.DIRICHLET:
+        return 1.0
+    W0 = olmep.constant_weights(p)[:, 0]
+    return max(float(np.sum(np.abs(W0[r]))) for r in range(1, p.n - 1))
 
 
 def ic_of(name, p, seed):
@@ -89,10 +105,69 @@ def test_harvest_scheme_weights_etdrk4(L, H, precision, name):
         assert weight_err(raw.cpu().numpy()[:, k], wraw[:, k]) <= tol(precision), k
 
 
+def raw_rows(R, dt):
+    """The oracle's stored layout from rows [n][6][n] (E, A, B, G, E2, P2): W[n][4][n] with the rows of
+    exp(dt L) and dt^k phi_k (k = 1..3), Wh[n][2][n].  The combinations invert alpha, beta, gamma:
+    phi_2 = (B + G) / dt, phi_3 = (B + 2 G) / (4 dt^2), phi_1 = A + 2 B + G."""
+    E, A, B, G = R[:, 0], R[:, 1], R[:, 2], R[:, 3]
+    W = np.stack([E, A + 2 * B + G, (B + G) * dt, 0.25 * (B + 2 * G) * dt * dt], axis=1)
+    return W, R[:, 4:6]
+
+
+def exact_rows(p):
+    """E, A, B, G, E2, P2 of every row class in exact rational arithmetic, rounded to FP64 at the end.
+    c0 = 0, so the local matrix and its augmented forms are nilpotent and their exponentials are finite
+    Taylor sums (the rows of dt^k phi_k as in Sec. 3.1); the FP64 products dt c_k / h^k are the only
+    rounded inputs."""
+    from fractions import Fraction
+    from oracle import exact
+    assert p.c0 == 0.0
+    n = p.n
+
+    def rows(dt, q, r):
+        X = exact.local_matrix(n, dt, p.h, p.c1, p.c2, p.c3)
+        M = [[Fraction(0)] * (n + q) for _ in range(n + q)]
+        for a in range(n):
+            M[a][:n] = X[a]
+        d = Fraction(dt)
+        M[n][r] = d
+        for j in range(1, q):
+            M[n + j][n + j - 1] = d
+        Ex = exact.expm_nilpotent(M)
+        return [Ex[r][:n]] + [Ex[n + k][:n] for k in range(q)]
+
+    out = []
+    dt = Fraction(p.dt)
+    for r in range(n):
+        w = rows(p.dt, 3, r)
+        w2 = [v / dt for v in w[2]]
+        w3 = [v / dt ** 2 for v in w[3]]
+        hh = rows(0.5 * p.dt, 1, r)
+        cls = [w[0], [a - 3 * b + 4 * c for a, b, c in zip(w[1], w2, w3)], [2 * b - 4 * c for b, c in zip(w2, w3)],
+               [4 * c - b for b, c in zip(w2, w3)], hh[0], hh[1]]
+        out.append([[float(v) for v in row] for row in cls])
+    return np.array(out)
+
+
+def oracle_steps(p, rows, u0, K):
+    """K steps of the oracle's ETDRK4 stepper on given rows [n][6][n]."""
+    W, Wh = raw_rows(rows, p.dt)
+    D = olmep.unit_D(p.n)
+    u = np.array(u0, dtype=np.float64)
+    for _ in range(K):
+        u = olmep.step(p, W, u, D, Wh)
+    return u
+
+
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("name", list(cases()))
 def test_etdrk4_step_and_trajectory(L, H, precision, name):
     p, seed = cases()[name]
+    kappa = wall_kappa(p)
+    if precision == "mixed" and kappa * 2.0 ** -24 > 1e-3:
+        # n = 13 next to a wall: kappa = 7.7e4, so the FP32 rounding of the state is amplified beyond any
+        # FP32 tolerance within a step (the FP32 form is outside its accuracy regime; FP64 runs the case)
+        pytest.skip(f"FP32 form with one-sided rows of l1 norm {kappa:.3g}")
     u0 = ic_of(name, p, seed)
     if p.bc == wl.DIRICHLET:
         u0[0], u0[-1] = p.bc_lo, p.bc_hi
@@ -101,22 +176,36 @@ def test_etdrk4_step_and_trajectory(L, H, precision, name):
     dt_ = L.state_dtype(precision)
     W = torch.empty(p.n, 6, p.n, dtype=dt_, device="cuda")
     L.lmep_harvest_scheme_weights(H, grid_of(p), op_of(p), p.dt, "etdrk4", W, precision)
+    Wg = W.cpu().numpy().astype(np.float64)
     u = torch.tensor(u0, dtype=dt_, device="cuda")
     work = torch.empty_like(u)
     u1 = u.clone()
     L.lmep_step(H, grid_of(p), op_of(p), "etdrk4", p.nonlin, p.dt, W, u1, work, 1, precision)
     L.lmep_sync_status(H)
-    assert rel_linf(u1.cpu().numpy(), olmep.run(p, u0, 1)) <= tol(precision)
+    got1 = u1.cpu().numpy()
+    # the apply: the oracle's stepper on the GPU's own rows
+    assert rel_linf(got1, oracle_steps(p, Wg, u0, 1)) <= tol(precision)
     L.lmep_step(H, grid_of(p), op_of(p), "etdrk4", p.nonlin, p.dt, W, u, work, p.steps, precision)
     L.lmep_sync_status(H)
+    gotK = u.cpu().numpy()
     # K-step bound: K x the one-step tolerance, times (FP32 form) the largest l1 norm kappa of an updated
     # row of exp(dt L): next to a Dirichlet wall the one-sided rows (kappa = 48 at n = 9, mu = 0.5)
     # multiply the FP32 rounding of the state at every step; kappa = 1 on periodic and Neumann grids
-    kappa = 1.0
-    if precision == "mixed" and p.bc == wl.DIRICHLET:
-        W0 = olmep.constant_weights(p)[:, 0]
-        kappa = max(float(np.sum(np.abs(W0[r]))) for r in range(1, p.n - 1))
-    assert rel_linf(u.cpu().numpy(), olmep.run(p, u0)) <= tol(precision) * p.steps * kappa
+    if precision == "fp64":
+        kappa = 1.0
+    one, traj = olmep.run(p, u0, 1), olmep.run(p, u0)
+    e1, eK = rel_linf(got1, one), rel_linf(gotK, traj)
+    if e1 <= tol(precision) and eK <= tol(precision) * p.steps * kappa:
+        return
+    # FP64 on walled grids at n = 13: the one-sided rows next to a wall have l1 norms up to 8e4 (exp(dt L))
+    # and both FP64 harvests (Pade on the rounded local matrices) carry errors of that order times the
+    # rounding unit; the exact rational rows decide, and the GPU must be at least as close to the steps
+    # on them as the oracle is
+    assert precision == "fp64" and p.bc == wl.DIRICHLET, (e1, eK)
+    ex = exact_rows(p)
+    x1, xK = oracle_steps(p, ex, u0, 1), oracle_steps(p, ex, u0, p.steps)
+    assert rel_linf(got1, x1) <= max(2 * rel_linf(one, x1), tol(precision)), (rel_linf(got1, x1), rel_linf(one, x1))
+    assert rel_linf(gotK, xK) <= max(2 * rel_linf(traj, xK), tol(precision) * p.steps)
 
 
 @pytest.mark.parametrize("precision", PRECS)
@@ -147,3 +236,33 @@ def test_etdrk4_rejections(L, H):
     with pytest.raises(L.LmepError):                            # ETD1 with N(u) = -u u_x on Neumann
         L.lmep_step(H, grid_of(q.with_(bc=wl.NEUMANN)), op_of(q), "etd1", "burgers", q.dt,
                     torch.zeros(13, 2, 13, dtype=torch.float64, device="cuda"), u, torch.empty_like(u), 1, "fp64")
+
+
+@pytest.mark.parametrize("precision", PRECS)
+def test_etdrk4_full_size_sampled(L, H, precision):
+    """The benchmark's ETDRK4 workload (periodic viscous Burgers, nu = 0.03, N = 2^22, n = 13, nu dt / h^2 =
+    0.5), one step in the launch configuration the benchmark times, on sampled points: a point's update
+    depends on the 4 (r_s + r_N) = 48 values on each side, so the oracle's periodic step on a 161-point
+    segment of the same spacing centred on it gives its exact value at the centre."""
+    p = wl.burgers_etd(N=1 << 22, n=13, nu=0.03, dt=0.0, steps=1)
+    p = p.with_(dt=0.5 * p.h * p.h / p.c2)
+    u0 = wl.burgers_etd_ic(p)
+    if precision == "mixed":
+        u0 = u0.astype(np.float32).astype(np.float64)
+    dt_ = L.state_dtype(precision)
+    W = torch.empty(p.n, 6, p.n, dtype=dt_, device="cuda")
+    L.lmep_harvest_scheme_weights(H, grid_of(p), op_of(p), p.dt, "etdrk4", W, precision)
+    u = torch.tensor(u0, dtype=dt_, device="cuda")
+    L.lmep_step(H, grid_of(p), op_of(p), "etdrk4", p.nonlin, p.dt, W, u, torch.empty_like(u), 1, precision)
+    L.lmep_sync_status(H)
+    got = u.cpu().numpy().astype(np.float64)
+    R = 80
+    M = 2 * R + 1
+    seg = p.with_(N=M, b=p.a + M * p.h)
+    rng = np.random.default_rng(3)
+    picks = np.r_[0, 1, 47, 2047, 2048, 2049, p.N // 2, p.N - 49, p.N - 1, rng.integers(0, p.N, 15)]
+    scale = float(np.max(np.abs(u0)))
+    for i in picks:
+        idx = (int(i) + np.arange(-R, R + 1)) % p.N
+        want = olmep.run(seg, u0[idx], 1)[R]
+        assert abs(got[int(i)] - want) <= tol(precision) * scale, (int(i), got[int(i)], want)
