@@ -63,9 +63,38 @@ NU = 1e-6
 PI_M = {3: 2, 5: 3, 7: 4, 9: 5, 13: 6}          # matrix products of Pade [m/m] (Higham 2005)
 P32_NOMINAL = 152 * 128 * 2 * 2.07e9             # FP32 FMA lanes x 2 x max SM clock
 P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
-# DRAM bytes (read + write) per launch of the batched Allen-Cahn apply, k_apply_stream<float, ETDRK2, 9>,
-# from one ncu capture of the tile 1024 / block 128 launch shape (2026-11, the kernel unchanged since).
-TRAFFIC_K_APPLY_STREAM_AC = 253.765632e6 + 196.658688e6
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of a kernel, from one capture of its
+# profile case, with a hash of the sources that build the kernel at that capture: reported only while the
+# sources still hash to it (a changed kernel reports null until captured again).
+#   frozen_set: one step of the nine-instance set (`--profile-case set 128 1`): the lean launch
+#     2,586,112 + 256 B and the fallback 72,192 B.
+#   apply_stream_ac: one step of the 4096-instance Allen-Cahn ETDRK2 batch (`--profile-case ac 1024 64`):
+#     253,727,232 B read + 197,143,808 B written.
+TRAFFIC = {
+    "apply_stream_ac": (450_871_040, "163250995021b624",
+                        ("lmep_apply_stream.cu", "lmep_stream.cuh", "lmep_device.cuh")),
+    "frozen_set": (2_658_560, "8b2b7ce633b692c7",
+                   ("lmep_frozen_set.cuh", "lmep_frozen_set.cu", "lmep_set_fb_f32.cu", "lmep_warp_kernel.cuh",
+                    "lmep_device.cuh", "lmep_stream.cuh")),
+}
+
+
+def sources_sha(names) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_15964_gb300", "csrc", nm),
+                  "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(key: str):
+    """The captured DRAM bytes of `key`, or None once its sources have changed (or were never captured)."""
+    if key not in TRAFFIC:
+        return None
+    nbytes, sha, names = TRAFFIC[key]
+    return nbytes if sources_sha(names) == sha else None
 
 
 def workload_config(rank_seed: int = 0) -> dict:
@@ -567,8 +596,8 @@ def allen_cahn_main(args, rank, world, local_rank, cores):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": allen_cahn_config(B, batch),
             "error": {"vs": "FP64 oracle, one step, the cpu_baseline instances", "rel_linf": err},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_K_APPLY_STREAM_AC,
-                         "traffic_unit": "bytes per launch (ncu, tile 1024 / block 128 capture; below the "
+                         "frac": achieved / peak, "traffic": traffic_of("apply_stream_ac"),
+                         "traffic_unit": "bytes per launch (ncu, tile 1024 / block 64 capture; below the "
                                          "algorithmic bytes because part of u+ is still in L2 at the end)",
                          "peak_source": peak_src,
                          "kernel": "k_apply_stream<float, ETDRK2, n = 9> (one persistent launch per step)",
@@ -1597,9 +1626,11 @@ def main():
                                        "Fractions) at 40 points of the n = 13, CFL 4 instance, first step",
                                "rel_linf": err_exact}},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / p32, "traffic": None,
-                     "traffic_unit": "bytes per step (ncu dram__bytes_read.sum + dram__bytes_write.sum); null until "
-                                     "captured for this kernel",
+                     "frac": achieved / p32, "traffic": traffic_of("frozen_set"),
+                     "traffic_unit": "bytes per step, both launches (ncu dram__bytes_read.sum + "
+                                     "dram__bytes_write.sum of one capture at launch shape 128 x 1; null once the "
+                                     "kernels' sources differ from those captured); algorithmic bytes per step: "
+                                     "4,718,592 (u in, u+ out, FP32); the capture's output stays in L2",
                      "kernel": "k_frozen_set<float> + k_frozen_set_fallback<float> (the two launches of one step "
                                "of all nine instances; the fallback finds no rejected point on this workload)",
                      "note": "FP32-equivalent rate (F32 + F64 * P32/P64) / t of the algorithm's own FLOPs per step "

@@ -47,3 +47,17 @@ def test_adjoint_flops_by_route():
     assert bench.adj_flops(n, [2], [0]) == 6 * n * n + 14 * n
     assert bench.adj_flops(n, [13], [1]) == 2.0 * n ** 3 * 37 + 12.0 * n ** 3 + 4.0 * n
     assert bench.adj_flops(n, [2, 13], [0, 1]) == 6 * n * n + 14 * n + 2.0 * n ** 3 * 37 + 12.0 * n ** 3 + 4.0 * n
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    """A captured DRAM figure stays in the bench line only while the kernel's sources are those captured."""
+    import bench
+    for key, (nbytes, sha, names) in bench.TRAFFIC.items():
+        assert nbytes > 0 and len(sha) == 16 and names
+        assert bench.traffic_of(key) in (nbytes, None)
+    monkeypatch.setitem(bench.TRAFFIC, "probe", (123, "0" * 16, ("lmep_frozen_set.cu",)))
+    assert bench.traffic_of("probe") is None
+    sha = bench.sources_sha(("lmep_frozen_set.cu",))
+    monkeypatch.setitem(bench.TRAFFIC, "probe", (123, sha, ("lmep_frozen_set.cu",)))
+    assert bench.traffic_of("probe") == 123
+    assert bench.traffic_of("never_captured") is None
