@@ -248,7 +248,8 @@ typedef struct lmep_frozen_set_desc {
   const lmep_operator* ops_host;     /* [B]: frozen_adv != 0 */
   const double* dt_host;             /* [B]: > 0 */
   int32_t block;                     /* threads per CTA: 0 (default 256), 64, 128, 256 or 512 */
-  int32_t points_per_thread;         /* 0 (default 2), 1 or 2; a CTA updates block * this points */
+  int32_t points_per_thread;         /* 0 (default 2), 1, 2, 4 or 8; a CTA updates block * this points per
+                                        tile: 1 or 2 points per thread together, 4 / 8 as 1 / 2 four times */
 } lmep_frozen_set_desc;
 
 /* Bytes of the workspace of a set (instance records, tile table, exp(E)

@@ -612,7 +612,7 @@ lmep_status set_layout(const lmep_frozen_set_desc* d, int32_t precision, int32_t
   const int ppt = d->points_per_thread > 0 ? d->points_per_thread : 2;
   if (block != 64 && block != 128 && block != 256 && block != 512)
     return fail(LMEP_ERR_INVALID, "block must be 64, 128, 256 or 512");
-  if (ppt != 1 && ppt != 2) return fail(LMEP_ERR_INVALID, "points_per_thread must be 1 or 2");
+  if (ppt != 1 && ppt != 2 && ppt != 4 && ppt != 8) return fail(LMEP_ERR_INVALID, "points_per_thread must be 1, 2, 4 or 8");
   std::vector<int32_t> n(size_t(d->B));
   std::vector<int64_t> N(size_t(d->B));
   int64_t off = 0;

@@ -68,7 +68,7 @@ __device__ __forceinline__ void setup_one(const WarpJob& job, const SetInst& in,
 }
 
 template <typename PT>
-__global__ void __launch_bounds__(32) k_frozen_set_setup(const WarpJob* jobs, const SetInst* inst, double* exps,
+__global__ void __launch_bounds__(32) k_frozen_set_setup(const WarpJob* jobs, SetInst* inst, double* exps,
                                                          void* tab, int32_t* ok) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* Dh = reinterpret_cast<double*>(smem);
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(32) k_frozen_set_setup(const WarpJob* jobs, co
     case 13: setup_one<13, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
     default: setup_one<15, PT>(job, inst[b], Dh, w, e, t, ok, lane); break;
   }
+  if (lane == 0) inst[b].ok = ok[b];  // staged with the record by the lean kernel (lane 0 wrote ok[b])
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -98,8 +99,12 @@ cudaError_t allow_smem(K kernel, size_t smem) {
 
 
 // The lean kernel of a set and its shared memory: two staging buffers (table, tile and halo).
+// points per thread and tile: 1 or 2 together in registers, or 4 / 8 as 1 / 2 together, four times in turn
 template <typename PT>
-auto set_kernel(int ppt) { return ppt == 2 ? k_frozen_set<PT, 2> : k_frozen_set<PT, 1>; }
+auto set_kernel(int ppt) {
+  return ppt == 8 ? k_frozen_set<PT, 2, 4>
+                  : (ppt == 4 ? k_frozen_set<PT, 1, 4> : (ppt == 2 ? k_frozen_set<PT, 2, 1> : k_frozen_set<PT, 1, 1>));
+}
 template <typename PT>
 size_t set_smem(const SetLayout& L) {
   return 2 * (size_t(TAB_MAX) + size_t(L.block) * L.ppt + 2 * DMAX) * sizeof(PT);
@@ -247,7 +252,7 @@ cudaError_t frozen_set_refresh(void* ws, const SetLayout& L, cudaStream_t s) {
   char* base = static_cast<char*>(ws);
   const size_t smem = DH_BYTES + Ws<double>::BYTES;
   const WarpJob* jobs = reinterpret_cast<const WarpJob*>(base + L.jobs);
-  const SetInst* inst = reinterpret_cast<const SetInst*>(base + L.inst);
+  SetInst* inst = reinterpret_cast<SetInst*>(base + L.inst);
   double* exps = reinterpret_cast<double*>(base + L.exps);
   int32_t* ok = reinterpret_cast<int32_t*>(base + L.ok);
   if (L.mixed) {

@@ -17,6 +17,7 @@ struct alignas(16) SetInst {
   int64_t list_off;  // first entry of its rejected-point list
   int64_t tab;       // first element of its table (product type): exp(E) rows, stride NP(n), then R_j
   int32_t route;     // 0: factorised rows first; 1: every point through the fallback
+  int32_t ok;        // 1 when the instance's exp(E) table is finite (written by the set-up kernel)
 };
 static_assert(sizeof(SetInst) % 16 == 0, "SetInst is copied as 16-byte vectors");
 
@@ -158,7 +159,7 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
   const int tp = int(blockDim.x) * PPT;
   const int len = N - t0 < tp ? N - t0 : tp;
   ST* out = static_cast<ST*>(a.out) + in.off;
-  const bool fact = in.route == 0 && a.ok[b] != 0;
+  const bool fact = in.route == 0 && in.ok != 0;
   PT l[PPT][D];
   int ls[PPT];
   bool take[PPT], live[PPT], vld[PPT];
@@ -281,8 +282,11 @@ __device__ __forceinline__ void set_tile(const SetArgs& a, const SetInst& in, in
   }
 }
 
-// The tiles tile .. end - 1 of a CTA, staged two buffers deep.
-template <typename PT, int PPT>
+// The tiles tile .. end - 1 of a CTA, staged two buffers deep.  A tile holds
+// SEQ sub-tiles of blockDim.x * PPT points, computed in turn (PPT points per
+// thread together in registers, SEQ times), so that the per-tile work of the
+// CTA (staging, barrier, records) is shared by SEQ * PPT points per thread.
+template <typename PT, int PPT, int SEQ>
 __device__ __forceinline__ void set_tiles(const SetArgs& a, int tile, const int end, PT* buf, SetInst* s_in,
                                           const int stride, const int tp, unsigned& bad) {
   SetTile cur = a.tiles[tile];
@@ -307,14 +311,21 @@ __device__ __forceinline__ void set_tiles(const SetArgs& a, int tile, const int 
     const PT* sT = buf + bi * stride;
     const PT* su = sT + TAB_MAX;
     const SetInst& in = s_in[bi];
-    switch (cur.n) {
-      case 3: set_tile<3, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      case 5: set_tile<5, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      case 7: set_tile<7, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      case 9: set_tile<9, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      case 11: set_tile<11, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      case 13: set_tile<13, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
-      default: set_tile<15, PT, PPT>(a, in, cur.b, cur.t0, sT, su, bad); break;
+    const int sub = int(blockDim.x) * PPT;
+#pragma unroll 1
+    for (int q = 0; q < SEQ; ++q) {
+      const int t0 = cur.t0 + q * sub;
+      if (t0 >= cur.N) break;  // the instance's ragged last tile (uniform over the CTA)
+      const PT* suq = su + q * sub;
+      switch (cur.n) {
+        case 3: set_tile<3, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        case 5: set_tile<5, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        case 7: set_tile<7, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        case 9: set_tile<9, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        case 11: set_tile<11, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        case 13: set_tile<13, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+        default: set_tile<15, PT, PPT>(a, in, cur.b, t0, sT, suq, bad); break;
+      }
     }
     if (!has_nxt) break;
     cur = nxt;
@@ -331,11 +342,11 @@ __device__ __forceinline__ void set_tiles(const SetArgs& a, int tile, const int 
 // registers, so the loads of a tile overlap the arithmetic of the previous one.
 // One point per thread: at most 64 registers, so that 8 CTAs of 128 threads
 // (or 2 of 512) fit on an SM.
-template <typename PT, int PPT>
+template <typename PT, int PPT, int SEQ>
 __global__ void __launch_bounds__(512, PPT == 1 ? 2 : 1) k_frozen_set(SetArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(16) SetInst s_in[2];
-  const int tp = int(blockDim.x) * PPT;
+  const int tp = int(blockDim.x) * PPT * SEQ;
   const int stride = TAB_MAX + tp + 2 * DMAX;  // elements per buffer (a multiple of 16)
   PT* buf = reinterpret_cast<PT*>(smem);
   // the tile records and instance records are read-only; the state and the
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(512, PPT == 1 ? 2 : 1) k_frozen_set(SetArgs a)
   int tile = a.starts[blockIdx.x];
   const int end = a.starts[blockIdx.x + 1];
   unsigned bad = 0;
-  if (tile < end) set_tiles<PT, PPT>(a, tile, end, buf, s_in, stride, tp, bad);
+  if (tile < end) set_tiles<PT, PPT, SEQ>(a, tile, end, buf, s_in, stride, tp, bad);
   if (bad) atomicOr(a.flags, 1u);
 }
 

@@ -28,7 +28,8 @@ from . import (Grid, Handle, LmepError, Operator, frozen_set_offsets, lmep_froze
                lmep_frozen_set_refresh, lmep_frozen_set_step_once, lmep_frozen_set_workspace_bytes,
                lmep_set_expm_method, lmep_step, state_dtype)
 
-SHAPES = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1), (256, 2), (512, 1)]
+SHAPES = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1), (256, 2), (512, 1), (64, 4), (128, 4), (256, 4), (64, 8),
+          (128, 8)]
 
 
 @dataclass

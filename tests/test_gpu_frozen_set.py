@@ -66,7 +66,7 @@ def make_set(L, probs, precision, method="auto", block=0, ppt=0, handle=None):
 
 @pytest.mark.parametrize("precision", PRECS)
 @pytest.mark.parametrize("method", ["auto", "series", "pade"])
-@pytest.mark.parametrize("block,ppt", [(0, 0), (64, 1), (512, 1), (128, 2)])
+@pytest.mark.parametrize("block,ppt", [(0, 0), (64, 1), (512, 1), (128, 2), (64, 4), (128, 8)])
 def test_set_equals_single_instance_steps(L, precision, method, block, ppt):
     if method == "pade" and (block, ppt) != (0, 0):
         pytest.skip("the Pade route does not depend on the launch shape of the lean kernel")
