@@ -295,7 +295,9 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
 
     fis = [inst_of(p) for _, _, p in insts]
     shape, shape_ms = tune(fis, [u0[k] for k in keys], "mixed", "auto", use_cache=False, handle=h)
-    results = {"shape": {"block": shape[0], "points_per_thread": shape[1], "ms_per_step": shape_ms}}
+    shape64, shape64_ms = tune(fis, [u0[k] for k in keys], "fp64", "auto", use_cache=False, handle=h)
+    results = {"shape": {"block": shape[0], "points_per_thread": shape[1], "ms_per_step": shape_ms},
+               "shape_fp64": {"block": shape64[0], "points_per_thread": shape64[1], "ms_per_step": shape64_ms}}
     legs = (("mixed", "mixed", "auto", True), ("fp64", "fp64", "auto", True), ("pade", "mixed", "pade", True),
             ("unfused", "mixed", "auto", False))
     for key, prec, method, fused in legs:
@@ -303,8 +305,9 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
             steps = 200                      # the Pade route is ~100x slower; its rate needs few steps
         else:
             steps = args.steps
-        fs = FrozenSet(fis, precision=prec, method=method, handle=h, fused=fused, block=shape[0],
-                       points_per_thread=shape[1])
+        shp = shape64 if prec == "fp64" else shape
+        fs = FrozenSet(fis, precision=prec, method=method, handle=h, fused=fused, block=shp[0],
+                       points_per_thread=shp[1])
         fs.load([u0[k] for k in keys])
         # route statistics (m, s, a) of every point at the initial state, from the kernel itself
         stats = {}
@@ -797,8 +800,8 @@ def adjoint_main(args, rank, world, local_rank, cores):
     line = {"metric": "gradient point-steps/s (forward + reverse)", "value": pts / (total * 1e-3),
             "unit": "point-steps/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 forward + f64 derivatives (closed form of the factorised rows; Pade Frechet where "
-                     "the bound is large)", "data": "synthetic", "config": adjoint_config(B, K),
+            "dtype": "f32 forward and derivative rows on window residuals, f64 sums (closed form of the "
+                     "factorised rows; Pade Frechet in f64 where the bound is large)", "data": "synthetic", "config": adjoint_config(B, K),
             "forward_ms": t_fwd, "reverse_ms": t_bwd,
             "error": {"vs": "FP64 oracle gradient, one step, 4 instances of N = 4096", "rel": err},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": P64_NOMINAL / 1e12,
@@ -821,7 +824,7 @@ def adjoint_main(args, rank, world, local_rank, cores):
 def adjoint_full_main(args, rank, world, local_rank, cores):
     """Configuration 5 at its stated size: 256 initial states x N = 262144, 2048 steps, a checkpoint every
     64 steps; one gradient of J = h/2 sum_b ||u_b(T) - u*_b||^2 with respect to the initial states and nu
-    through torch.autograd (FP32 forward, FP64 derivatives), timed with CUDA events and with the clocks
+    through torch.autograd (FP32 forward and derivative rows, FP64 sums), timed with CUDA events and with the clocks
     sampled; then, on the first four instances, central differences of the FP64 GPU forward along a seeded
     direction v in the initial states, (J(x0 + e v) - J(x0 - e v)) / 2e, against <dJ/dx0, v> of the timed
     run and of the FP64 adjoint, and the same in nu."""
@@ -898,7 +901,7 @@ def adjoint_full_main(args, rank, world, local_rank, cores):
     line = {"metric": "gradient point-steps/s (forward + reverse)", "value": ADJ_N * B * K / (total * 1e-3),
             "unit": "point-steps/s", "n_gpus": 1, "steps": K, "warmup": 0, "ms_per_step": total / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 forward + f64 derivatives", "data": "synthetic",
+            "dtype": "f32 forward and derivative rows, f64 dJ/dnu sum", "data": "synthetic",
             "config": {"workload": f"configuration 5 at full size: {B} x N = {ADJ_N}, {K} steps, checkpoint every "
                                    f"{C}, n = {ADJ_NS}, CFL {ADJ_CFL}, nu = {NU}, J = h/2 sum ||u(T) - u*||^2"},
             "forward_ms": fwd_ms, "reverse_ms": rev_ms, "clocks": clk,
@@ -1205,7 +1208,7 @@ def cfg5_adjoint(L, B: int = 8, K: int = 4):
     ms = min(_timed_ms(once) for _ in range(3))
     L.lmep_sync_status(solver.handle)
     return {"workload": f"adjoint of frozen Burgers, {B} x N = {ADJ_N}, n = 9, CFL 2, nu = 1e-6, {K} steps "
-                        "forward + reverse (checkpoint every 2), FP32 forward, FP64 derivatives",
+                        "forward + reverse (checkpoint every 2), FP32 forward and derivative rows, FP64 dJ/dnu sum",
             "gradient_point_steps_per_s": ADJ_N * B * K / (ms * 1e-3), "ms": ms}
 
 
@@ -1612,6 +1615,7 @@ def main():
                            "instance's exp(E), one launch) per step, as the configuration's 1000-step run "
                            "spends it", "launch_shape": res["shape"]},
         "fp64": {"value": amortised(fp), "ms_per_step": fp["ms_per_step"], "setup_ms": fp["setup_ms"],
+                 "launch_shape": res["shape_fp64"],
                  "dtype": "f64"},
         "pade_route": {"value": amortised(res["pade"]), "ms_per_step": res["pade"]["ms_per_step"],
                        "steps": res["pade"]["steps"],

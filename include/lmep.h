@@ -281,6 +281,10 @@ LMEP_API lmep_status lmep_frozen_set_step_once(lmep_handle* h, const void* works
  * with dF_i/du_i containing the row of the Frechet derivative of the local
  * exponential in the direction dX/du_i = -dt frozen_adv D1, and dF_i/dnu the
  * one in the direction dX/dnu = dt D2 (Higham, Functions of Matrices, Thm 3.6).
+ * Where the factorised form holds (the default route) these rows are closed
+ * forms of l(z)^T exp(E); the FP32 form evaluates them in FP32 on the window's
+ * values minus their linear interpolant (formed in FP64, its contribution
+ * added exactly) and sums dnu in FP64; the Pade Frechet rows run in FP64.
  * scratch_dev: at least lmep_adjoint_scratch_bytes(g, precision) bytes.
  * u_dev, lam_next_dev, lam_dev: state dtype; dnu_dev: double[1]. */
 LMEP_API lmep_status lmep_adjoint_scratch_bytes(const lmep_grid* g, int32_t precision, size_t* bytes_out);

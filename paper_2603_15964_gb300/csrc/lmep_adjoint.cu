@@ -23,12 +23,15 @@
 // one point per thread (k_adjoint_fact); points whose bound
 // sum_j |l_j| |row j of exp(E)|_1 exceeds 16 are marked and take the Pade
 // derivatives in k_adjoint_points.
-// Everything in this file runs in FP64; lam is stored in the state dtype.
+// The Pade Frechet path runs in FP64; the factorised path in the product type of
+// the state (FP64, or FP32 for the FP32 form) with dnu summed in FP64; lam is
+// stored in the state dtype.
 // The exact re-centring of the forward step (row r of exp(X) equals row r-k
 // of exp(X + k Dh1)) shifts X by a constant matrix, so the directions E are
 // unchanged and the same identity holds for L.
 #include <climits>
 #include <cstdio>
+#include <type_traits>
 
 #include "lmep_device.cuh"
 #include "lmep_internal.h"
@@ -328,12 +331,25 @@ struct AdjTables {
   double rs[D];
   double d2ex[D * D];
 };
+// The FP32 form's tables (exp(E), its absolute row sums and Dh2 exp(E) rounded
+// to FP32): with the loops unrolled, the rows are constant-bank operands.
+template <int D>
+struct AdjTablesF {
+  float ex[D * D];
+  float rs[D];
+  float d2ex[D * D];
+};
+template <int D, typename ST>
+using AdjTab = typename std::conditional<sizeof(ST) == 4, AdjTablesF<D>, AdjTables<D>>::type;
 
 // One point per thread: the row w, g_u = dw/du_i . u[window] and the window
 // offset into the scratch arrays of k_adjoint_gather, lam+_i dw/dnu . u[window]
 // into dnu; a point whose bound exceeds the threshold gets st_out = ADJ_MARK.
+// The window and the departure position z are formed in FP64; the FP32 form
+// (ST = float) then takes the weights, their derivatives and the three rows in
+// FP32 (the precision of its forward rows), and every form sums dnu in FP64.
 template <int D, typename ST>
-__global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTables<D> t, const ST* __restrict__ u,
+__global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t, const ST* __restrict__ u,
                                                       const ST* __restrict__ lam_next, ST* __restrict__ Wout,
                                                       ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
                                                       double* dnu) {
@@ -358,49 +374,65 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTables<D> t,
     const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
     const int64_t st = window_start(i, p.N, n, p.bc, k);
     const double z = double(i - st) + p.dt * (p.c1 - p.fa * ui) / p.h;
+    using CT = ST;  // arithmetic type of the rows
+    const CT zc = CT(z);
     // Lagrange weights l_j(z) and l_j'(z) by prefix and suffix products carried with
     // their derivatives (exact at the nodes)
-    double suf[D], sufd[D];
-    suf[D - 1] = 1.0;
-    sufd[D - 1] = 0.0;
+    CT suf[D], sufd[D];
+    suf[D - 1] = CT(1);
+    sufd[D - 1] = CT(0);
 #pragma unroll
     for (int j = D - 1; j > 0; --j) {
-      sufd[j - 1] = fma(sufd[j], z - double(j), suf[j]);
-      suf[j - 1] = suf[j] * (z - double(j));
+      sufd[j - 1] = fma(sufd[j], zc - CT(j), suf[j]);
+      suf[j - 1] = suf[j] * (zc - CT(j));
     }
-    double l[D], ld[D];
-    double pre = 1.0, pred = 0.0, bound = 0.0;
+    CT l[D], ld[D];
+    CT pre = CT(1), pred = CT(0), bound = CT(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      const double c = lagrange_den(D, j);
+      const CT c = CT(lagrange_den(D, j));
       l[j] = pre * suf[j] * c;
       ld[j] = fma(pred, suf[j], pre * sufd[j]) * c;
-      bound = fma(fabs(l[j]), t.rs[j], bound);
-      pred = fma(pred, z - double(j), pre);
-      pre *= z - double(j);
+      bound = fma(abs(l[j]), t.rs[j], bound);
+      pred = fma(pred, zc - CT(j), pre);
+      pre *= zc - CT(j);
     }
-    if (!(bound <= 16.0)) {
+    if (!(bound <= CT(16))) {
       st_out[it] = ADJ_MARK;
       continue;
     }
-    double gu = 0.0, gn = 0.0;
+    // g_u = l'(z)^T exp(E) u and g_nu = l(z)^T Dh2 exp(E) u are (first and
+    // second) differences of the window's values, far smaller than the values.
+    // The first row maps the constant 1 to 0 and the node index q to 1, the
+    // second maps both to 0 (exp(E) keeps polynomials of degree 1, Lagrange
+    // interpolation reproduces them), so both are taken on the residual
+    // r_q = u_q - (u_0 + s q) of the window's linear interpolant (formed in
+    // FP64), the linear part adding exactly s to g_u: in the FP32 form the
+    // products then round only the small residual.
+    double s_lin = 0.0, u_lin = 0.0;
+    if constexpr (sizeof(CT) == 4) {
+      u_lin = double(ub[grid_index(st, p.N, p.bc)]);
+      s_lin = (double(ub[grid_index(st + D - 1, p.N, p.bc)]) - u_lin) / double(D - 1);
+    }
+    CT gu = CT(0), gn = CT(0);
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      double w = 0.0, wu = 0.0, wn = 0.0;
+      CT w = CT(0), wu = CT(0), wn = CT(0);
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         w = fma(l[j], t.ex[j * D + q], w);
         wu = fma(ld[j], t.ex[j * D + q], wu);
         wn = fma(l[j], t.d2ex[j * D + q], wn);
       }
-      const double uq = double(ub[grid_index(st + q, p.N, p.bc)]);
-      Wout[it * n + q] = ST(e0 * w);
+      const double uqd = double(ub[grid_index(st + q, p.N, p.bc)]);
+      const CT uq = sizeof(CT) == 4 ? CT(uqd - fma(s_lin, double(q), u_lin)) : CT(uqd);
+      Wout[it * n + q] = ST(CT(e0) * w);
       gu = fma(wu, uq, gu);
       gn = fma(wn, uq, gn);
     }
-    gu_out[it] = ST(e0 * su * gu);
+    gu_out[it] = ST(e0 * su * (double(gu) + s_lin));
     st_out[it] = int32_t(st - i);
-    dnu_acc = fma(double(lam_next[it]), e0 * snu * gn, dnu_acc);
+    dnu_acc = fma(double(lam_next[it]), e0 * snu * double(gn), dnu_acc);
   }
   dnu_acc = warp_sum(dnu_acc);
   if ((threadIdx.x & 31) == 0 && dnu_acc != 0.0) atomicAdd(dnu, dnu_acc);
@@ -447,10 +479,11 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
   int32_t* st = reinterpret_cast<int32_t*>(gu + items);
   int fix = 0;
   if (sl) {
-    AdjTables<D> t;
-    for (int e = 0; e < D * D; ++e) t.ex[e] = sl[e];
-    for (int j = 0; j < D; ++j) t.rs[j] = sl[D * D + j];
-    for (int e = 0; e < D * D; ++e) t.d2ex[e] = sl[D * D + D + e];
+    AdjTab<D, ST> t;
+    using TT = typename std::remove_reference<decltype(t.ex[0])>::type;
+    for (int e = 0; e < D * D; ++e) t.ex[e] = TT(sl[e]);
+    for (int j = 0; j < D; ++j) t.rs[j] = TT(sl[D * D + j]);
+    for (int e = 0; e < D * D; ++e) t.d2ex[e] = TT(sl[D * D + D + e]);
     int64_t gf = (items + 127) / 128;
     if (gf > int64_t(device_info().sms) * 16) gf = int64_t(device_info().sms) * 16;
     k_adjoint_fact<D, ST><<<int(gf), 128, 0, s>>>(p, t, static_cast<const ST*>(u), static_cast<const ST*>(lam_next),

@@ -128,3 +128,21 @@ def test_gradient_matches_oracle_across_configs(L, precision, n, cfl, nu, N, ste
     err_u = np.max(np.abs(gu - want_u)) / np.max(np.abs(want_u))
     err_nu = abs(gnu - want_nu) / abs(want_nu)
     assert err_u <= tol and err_nu <= tol_nu, (err_u, err_nu, int(np.argmax(np.max(np.abs(gu - want_u), axis=0))))
+
+
+def test_fp32_form_gradient_on_a_fine_grid(L):
+    """Configuration 5's grid (N = 262144, n = 9, CFL 2, nu = 1e-6): the FP32 form's gradient against the
+    FP64 path's over 16 steps from the same FP32 initial state.  On this grid dw/du and dw/dnu applied to
+    the window are first and second differences some 1e-5 and 1e-9 of the values they difference, so an
+    FP32 evaluation that rounded the values themselves would lose them; the gradients must agree to the
+    FP32 forward's own precision (1e-3 relative, the two trajectories differ by FP32 rounding)."""
+    p = wl.burgers(N=262144, n=9, cfl=2.0, nu=1e-6, steps=16, departure_centring=True)
+    u0 = wl.burgers_ic(p.N, 0)[None, :].astype(np.float32).astype(np.float64)
+    target = wl.burgers_ic(p.N, 1000)[None, :]
+    _, g32, n32 = loss_and_grads(L, p, "mixed", 4, u0, target)
+    _, g64, n64 = loss_and_grads(L, p, "fp64", 4, u0, target)
+    v = np.random.default_rng(5).standard_normal(u0.shape)
+    d32, d64 = float(np.sum(g32 * v)), float(np.sum(g64 * v))
+    assert abs(d32 - d64) <= 1e-3 * abs(d64), (d32, d64)
+    assert np.max(np.abs(g32 - g64)) <= 1e-3 * np.max(np.abs(g64))
+    assert abs(n32 - n64) <= 1e-3 * abs(n64), (n32, n64)
