@@ -136,8 +136,10 @@ template <int D, typename ST>
 __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST* __restrict__ u,
                                                             const ST* __restrict__ lam_next, ST* __restrict__ Wout,
                                                             ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
-                                                            double* dnu, int fix) {
+                                                            double* dnu, int fix, const int* marks) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // after k_adjoint_fact: nothing marked (the usual case), so every CTA leaves
+  if (fix && *marks == 0) return;
   double* Dh = reinterpret_cast<double*>(smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int LA = AdjWs<D>::LDA;
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     split_index(it, p.N, p.batch, bb, i);
     const ST* ub = u + bb * p.N;
     if (dir && (i == 0 || i == p.N - 1)) {
-      for (int j = lane; j < n; j += 32) Wout[it * n + j] = ST(0);
+      for (int j = lane; j < n; j += 32) Wout[j * items + it] = ST(0);
       if (lane == 0) {
         gu_out[it] = ST(0);
         st_out[it] = 0;
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(32 * AW) k_adjoint_points(KParams p, const ST*
     if (lane < n) uj = double(ub[grid_index(st + lane, p.N, p.bc)]);
     const double gu = warp_sum(lane < n ? LU[0][hr * LA + lane] * uj : 0.0);
     const double gn = warp_sum(lane < n ? LU[1][hr * LA + lane] * uj : 0.0);
-    if (lane < n) Wout[it * n + lane] = ST(R[hr * LA + lane]);
+    if (lane < n) Wout[lane * items + it] = ST(R[hr * LA + lane]);
     __syncwarp();  // every lane has read this chunk's marks before lane 0 overwrites st_out
     if (lane == 0) {
       gu_out[it] = ST(gu);
@@ -352,7 +354,7 @@ template <int D, typename ST>
 __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t, const ST* __restrict__ u,
                                                       const ST* __restrict__ lam_next, ST* __restrict__ Wout,
                                                       ST* __restrict__ gu_out, int32_t* __restrict__ st_out,
-                                                      double* dnu) {
+                                                      double* dnu, int* marks) {
   const int n = p.n;
   const bool dir = p.bc == BC_DIRICHLET;
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
@@ -365,17 +367,29 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t
     split_index(it, p.N, p.batch, bb, i);
     const ST* ub = u + bb * p.N;
     if (dir && (i == 0 || i == p.N - 1)) {
-      for (int j = 0; j < n; ++j) Wout[it * n + j] = ST(0);
+      for (int j = 0; j < n; ++j) Wout[j * items + it] = ST(0);
       gu_out[it] = ST(0);
       st_out[it] = 0;
       continue;
     }
-    const double ui = double(ub[i]);
-    const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
-    const int64_t st = window_start(i, p.N, n, p.bc, k);
-    const double z = double(i - st) + p.dt * (p.c1 - p.fa * ui) / p.h;
     using CT = ST;  // arithmetic type of the rows
-    const CT zc = CT(z);
+    int64_t st;
+    CT zc;
+    if constexpr (sizeof(CT) == 4) {
+      // the FP32 form's window and departure position, as its forward step forms them
+      const float uf = float(ub[i]);
+      const int k = p.dep ? departure_shift_f32(uf, p, n) : 0;
+      st = window_start(i, p.N, n, p.bc, k);
+      const int r = int(i - st);
+      const float a1 = p.c1_f - p.fa_f * uf;
+      const int kr = int(fmaxf(float(r - (n - 1)), fminf(float(r), floorf(fmaf(-a1, p.dt_h_f, 0.5f)))));
+      zc = float(r - kr) + fmaf(a1, p.dt_h_f, float(kr));
+    } else {
+      const double ui = double(ub[i]);
+      const int k = p.dep ? departure_shift(ui, p.dt, p.h, n, p.dt_h) : 0;
+      st = window_start(i, p.N, n, p.bc, k);
+      zc = double(i - st) + p.dt * (p.c1 - p.fa * ui) / p.h;
+    }
     // Lagrange weights l_j(z) and l_j'(z) by prefix and suffix products carried with
     // their derivatives (exact at the nodes)
     CT suf[D], sufd[D];
@@ -399,20 +413,21 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t
     }
     if (!(bound <= CT(16))) {
       st_out[it] = ADJ_MARK;
+      atomicAdd(marks, 1);
       continue;
     }
     // g_u = l'(z)^T exp(E) u and g_nu = l(z)^T Dh2 exp(E) u are (first and
     // second) differences of the window's values, far smaller than the values.
     // The first row maps the constant 1 to 0 and the node index q to 1, the
     // second maps both to 0 (exp(E) keeps polynomials of degree 1, Lagrange
-    // interpolation reproduces them), so both are taken on the residual
-    // r_q = u_q - (u_0 + s q) of the window's linear interpolant (formed in
-    // FP64), the linear part adding exactly s to g_u: in the FP32 form the
-    // products then round only the small residual.
-    double s_lin = 0.0, u_lin = 0.0;
+    // interpolation reproduces them), so the FP32 form takes both on the
+    // residual r_q = (u_q - u_0) - s q of the window's linear interpolant (the
+    // difference u_q - u_0 rounds relative to itself), the linear part adding
+    // exactly s to g_u: the products then round only the small residual.
+    CT u_lin = CT(0), s_lin = CT(0);
     if constexpr (sizeof(CT) == 4) {
-      u_lin = double(ub[grid_index(st, p.N, p.bc)]);
-      s_lin = (double(ub[grid_index(st + D - 1, p.N, p.bc)]) - u_lin) / double(D - 1);
+      u_lin = CT(ub[grid_index(st, p.N, p.bc)]);
+      s_lin = (CT(ub[grid_index(st + D - 1, p.N, p.bc)]) - u_lin) * CT(1.0 / (D - 1));
     }
     CT gu = CT(0), gn = CT(0);
 #pragma unroll
@@ -424,16 +439,22 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t
         wu = fma(ld[j], t.ex[j * D + q], wu);
         wn = fma(l[j], t.d2ex[j * D + q], wn);
       }
-      const double uqd = double(ub[grid_index(st + q, p.N, p.bc)]);
-      const CT uq = sizeof(CT) == 4 ? CT(uqd - fma(s_lin, double(q), u_lin)) : CT(uqd);
-      Wout[it * n + q] = ST(CT(e0) * w);
+      const CT uv = CT(ub[grid_index(st + q, p.N, p.bc)]);
+      const CT uq = sizeof(CT) == 4 ? fma(-s_lin, CT(q), uv - u_lin) : uv;
+      Wout[q * items + it] = ST(CT(e0) * w);
       gu = fma(wu, uq, gu);
       gn = fma(wn, uq, gn);
     }
-    gu_out[it] = ST(e0 * su * (double(gu) + s_lin));
     st_out[it] = int32_t(st - i);
-    dnu_acc = fma(double(lam_next[it]), e0 * snu * double(gn), dnu_acc);
+    if constexpr (sizeof(CT) == 4) {
+      gu_out[it] = ST(CT(e0 * su) * (gu + s_lin));
+      dnu_acc += double(CT(lam_next[it]) * gn);  // scaled by e0 dt / h^2 below
+    } else {
+      gu_out[it] = ST(e0 * su * gu);
+      dnu_acc = fma(double(lam_next[it]), e0 * snu * double(gn), dnu_acc);
+    }
   }
+  if constexpr (sizeof(ST) == 4) dnu_acc *= e0 * snu;
   dnu_acc = warp_sum(dnu_acc);
   if ((threadIdx.x & 31) == 0 && dnu_acc != 0.0) atomicAdd(dnu, dnu_acc);
 }
@@ -461,7 +482,7 @@ __global__ void k_adjoint_gather(KParams p, const ST* __restrict__ lam_next, con
       const int64_t sti = i + st_rel[base + i];
       int64_t j = k - sti;
       if (!dir) j = grid_index(j, p.N, BC_PERIODIC);
-      if (j >= 0 && j < n) acc = fma(lam_next[base + i], W[(base + i) * n + j], acc);
+      if (j >= 0 && j < n) acc = fma(lam_next[base + i], W[j * items + base + i], acc);
     }
     if (!dir || (k >= 1 && k <= p.N - 2)) acc = fma(lam_next[kg], gu[kg], acc);
     lam[kg] = acc;
@@ -474,11 +495,17 @@ template <int D, typename ST>
 cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, void* lam, double* dnu,
                         void* scratch, unsigned* flags, cudaStream_t s, const double* sl) {
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
+  // scratch: the rows W[n][items] (row element j of every point together, so
+  // that one point per thread stores coalesced), g_u[items], window offsets
+  // st[items], then the count of points marked for the Pade derivatives
   ST* W = static_cast<ST*>(scratch);
   ST* gu = W + items * p.n;
   int32_t* st = reinterpret_cast<int32_t*>(gu + items);
+  int* marks = reinterpret_cast<int*>(st + items);
   int fix = 0;
   if (sl) {
+    cudaError_t em = cudaMemsetAsync(marks, 0, sizeof(int), s);
+    if (em != cudaSuccess) return em;
     AdjTab<D, ST> t;
     using TT = typename std::remove_reference<decltype(t.ex[0])>::type;
     for (int e = 0; e < D * D; ++e) t.ex[e] = TT(sl[e]);
@@ -487,7 +514,7 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
     int64_t gf = (items + 127) / 128;
     if (gf > int64_t(device_info().sms) * 16) gf = int64_t(device_info().sms) * 16;
     k_adjoint_fact<D, ST><<<int(gf), 128, 0, s>>>(p, t, static_cast<const ST*>(u), static_cast<const ST*>(lam_next),
-                                                  W, gu, st, dnu);
+                                                  W, gu, st, dnu, marks);
     cudaError_t ef = cudaGetLastError();
     if (ef != cudaSuccess) return ef;
     fix = 1;
@@ -503,7 +530,7 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
   const int64_t need = (items + 32 * AW - 1) / (32 * AW);  // chunks of 32 points per warp
   if (need < grid) grid = need;
   k1<<<int(grid), 32 * AW, smem, s>>>(p, static_cast<const ST*>(u), static_cast<const ST*>(lam_next), W, gu, st,
-                                      dnu, fix);
+                                      dnu, fix, marks);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int blk = 256;
