@@ -66,14 +66,14 @@ P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
 # DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of a kernel, from one capture of its
 # profile case, with a hash of the sources that build the kernel at that capture: reported only while the
 # sources still hash to it (a changed kernel reports null until captured again).
-#   frozen_set: one step of the nine-instance set (`--profile-case set 128 1`): the lean launch
-#     2,586,112 + 256 B and the fallback 72,192 B.
+#   frozen_set: one step of the nine-instance set (`--profile-case set 128 8`): the lean launch
+#     2,469,376 B and the fallback 72,192 B.
 #   apply_stream_ac: one step of the 4096-instance Allen-Cahn ETDRK2 batch (`--profile-case ac 1024 64`):
 #     253,727,232 B read + 197,143,808 B written.
 TRAFFIC = {
     "apply_stream_ac": (450_871_040, "163250995021b624",
                         ("lmep_apply_stream.cu", "lmep_stream.cuh", "lmep_device.cuh")),
-    "frozen_set": (2_658_560, "8b2b7ce633b692c7",
+    "frozen_set": (2_541_568, "de304222319da5ce",
                    ("lmep_frozen_set.cuh", "lmep_frozen_set.cu", "lmep_set_fb_f32.cu", "lmep_warp_kernel.cuh",
                     "lmep_device.cuh", "lmep_stream.cuh")),
 }
@@ -1632,7 +1632,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": p32 / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / p32, "traffic": traffic_of("frozen_set"),
                      "traffic_unit": "bytes per step, both launches (ncu dram__bytes_read.sum + "
-                                     "dram__bytes_write.sum of one capture at launch shape 128 x 1; null once the "
+                                     "dram__bytes_write.sum of one capture at launch shape 128 x 8; null once the "
                                      "kernels' sources differ from those captured); algorithmic bytes per step: "
                                      "4,718,592 (u in, u+ out, FP32); the capture's output stays in L2",
                      "kernel": "k_frozen_set<float> + k_frozen_set_fallback<float> (the two launches of one step "
