@@ -294,8 +294,11 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
         return out
 
     fis = [inst_of(p) for _, _, p in insts]
-    shape, shape_ms = tune(fis, [u0[k] for k in keys], "mixed", "auto", use_cache=False, handle=h)
-    shape64, shape64_ms = tune(fis, [u0[k] for k in keys], "fp64", "auto", use_cache=False, handle=h)
+    # shapes chosen as the legs are timed: lone steps after an L2 flush
+    shape, shape_ms = tune(fis, [u0[k] for k in keys], "mixed", "auto", steps=20, use_cache=False, handle=h,
+                           cold=True)
+    shape64, shape64_ms = tune(fis, [u0[k] for k in keys], "fp64", "auto", steps=20, use_cache=False, handle=h,
+                               cold=True)
     results = {"shape": {"block": shape[0], "points_per_thread": shape[1], "ms_per_step": shape_ms},
                "shape_fp64": {"block": shape64[0], "points_per_thread": shape64[1], "ms_per_step": shape64_ms}}
     legs = (("mixed", "mixed", "auto", True), ("fp64", "fp64", "auto", True), ("pade", "mixed", "pade", True),

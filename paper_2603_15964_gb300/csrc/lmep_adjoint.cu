@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t
   const bool dir = p.bc == BC_DIRICHLET;
   const int64_t items = p.N * (p.batch > 1 ? p.batch : 1);
   const double e0 = p.c0dt != 0.0 ? exp(p.c0dt) : 1.0;
-  const double su = -p.dt * p.fa / p.h, snu = p.dt / (p.h * p.h);
+  // d z / d u_i = -dt fa / h; the FP32 form takes it from its FP32 roundings (no FP64 division per thread)
+  const double su = sizeof(ST) == 4 ? double(-p.fa_f * p.dt_h_f) : -p.dt * p.fa / p.h;
   double dnu_acc = 0.0;
   for (int64_t it = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; it < items;
        it += int64_t(gridDim.x) * blockDim.x) {
@@ -451,10 +452,12 @@ __global__ void __launch_bounds__(128) k_adjoint_fact(KParams p, AdjTab<D, ST> t
       dnu_acc += double(CT(lam_next[it]) * gn);  // scaled by e0 dt / h^2 below
     } else {
       gu_out[it] = ST(e0 * su * gu);
-      dnu_acc = fma(double(lam_next[it]), e0 * snu * double(gn), dnu_acc);
+      dnu_acc = fma(double(lam_next[it]), e0 * (p.dt / (p.h * p.h)) * double(gn), dnu_acc);
     }
   }
-  if constexpr (sizeof(ST) == 4) dnu_acc *= e0 * snu;
+  if constexpr (sizeof(ST) == 4) {
+    if (dnu_acc != 0.0) dnu_acc *= e0 * (p.dt / (p.h * p.h));
+  }
   dnu_acc = warp_sum(dnu_acc);
   if ((threadIdx.x & 31) == 0 && dnu_acc != 0.0) atomicAdd(dnu, dnu_acc);
 }
@@ -511,7 +514,7 @@ cudaError_t run_adjoint(const KParams& p, const void* u, const void* lam_next, v
     for (int e = 0; e < D * D; ++e) t.ex[e] = TT(sl[e]);
     for (int j = 0; j < D; ++j) t.rs[j] = TT(sl[D * D + j]);
     for (int e = 0; e < D * D; ++e) t.d2ex[e] = TT(sl[D * D + D + e]);
-    int64_t gf = (items + 127) / 128;
+    int64_t gf = (items + 4 * 128 - 1) / (4 * 128);  // at least 4 points per thread: the prologue is shared
     if (gf > int64_t(device_info().sms) * 16) gf = int64_t(device_info().sms) * 16;
     k_adjoint_fact<D, ST><<<int(gf), 128, 0, s>>>(p, t, static_cast<const ST*>(u), static_cast<const ST*>(lam_next),
                                                   W, gu, st, dnu, marks);

@@ -172,14 +172,16 @@ def _cache_path() -> str:
 
 
 def tune(instances, arrays, precision: str = "mixed", method: str = "auto", steps: int = 10,
-         shapes=None, use_cache: bool = True, handle: Handle | None = None):
+         shapes=None, use_cache: bool = True, handle: Handle | None = None, cold: bool = False):
     """Time the fused step's launch shapes (threads per CTA, points per thread) on this GPU and return
     ((block, points_per_thread), {shape: ms per step}).  Each shape prepares its own workspace and is
-    timed with CUDA events over `steps` eager steps after two warm-up steps; the winner is cached per
-    (GPU, instance widths and sizes, precision, route) in $LMEP_AUTOTUNE_CACHE."""
+    timed with CUDA events after two warm-up steps: over `steps` eager steps back to back, or with
+    cold=True as the median of `steps` lone steps, each after a 256 MiB write that evicts the L2 (a
+    step of a caller that does other work between steps).  The winner is cached per (GPU, instance
+    widths and sizes, precision, route, timing) in $LMEP_AUTOTUNE_CACHE."""
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     key = (f"{props.name}|frozen_set|" + ",".join(f"{i.grid.n}:{i.grid.N}" for i in instances) +
-           f"|{precision}|{method}")
+           f"|{precision}|{method}" + ("|cold" if cold else ""))
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -193,17 +195,31 @@ def tune(instances, arrays, precision: str = "mixed", method: str = "auto", step
     handle = handle or Handle()
     timings = {}
     best, best_ms = None, float("inf")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if cold else None
     for block, ppt in shapes or SHAPES:
         fs = FrozenSet(instances, precision, method, handle, True, block, ppt)
         fs.load(arrays)
         fs.step(2)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fs.step(steps)
-        b.record()
-        b.synchronize()
-        ms = a.elapsed_time(b) / steps
+        if cold:
+            lone = []
+            for _ in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                fs.step(1)
+                b.record()
+                b.synchronize()
+                lone.append(a.elapsed_time(b))
+            ms = sorted(lone)[len(lone) // 2]
+        else:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fs.step(steps)
+            b.record()
+            b.synchronize()
+            ms = a.elapsed_time(b) / steps
         timings[f"{block}/{ppt}"] = ms
         if ms < best_ms:
             best, best_ms = (block, ppt), ms
