@@ -295,7 +295,7 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
 
     fis = [inst_of(p) for _, _, p in insts]
     # shapes chosen as the legs are timed: lone steps after an L2 flush
-    shape, shape_ms = tune(fis, [u0[k] for k in keys], "mixed", "auto", steps=20, use_cache=False, handle=h,
+    shape, shape_ms = tune(fis, [u0[k] for k in keys], "mixed", "auto", steps=40, use_cache=False, handle=h,
                            cold=True)
     shape64, shape64_ms = tune(fis, [u0[k] for k in keys], "fp64", "auto", steps=20, use_cache=False, handle=h,
                                cold=True)
@@ -401,6 +401,17 @@ def gpu_leg(args, rank: int, world: int, local_rank: int):
     nbytes = host_in.numel() * host_in.element_size()
     results["e2e"] = {"value": N_POINTS * len(insts) * e2e_steps * world / (e2e_total * 1e-3), "unit": UNIT,
                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    # the same round trip with the step reading and writing the pinned host buffers itself (unified
+    # addressing, no separate copy)
+    zc_ms = []
+    for _ in range(e2e_steps):
+        zc_ms += timed(lambda: L.lmep_frozen_set_step_once(fs.handle, fs.workspace, host_in, host_out), 1)
+        host_in.copy_(host_out)
+    zc_total = max_over_ranks(float(sum(zc_ms)), world)
+    results["e2e_zero_copy"] = {"value": N_POINTS * len(insts) * e2e_steps * world / (zc_total * 1e-3),
+                                "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                                "what": "lmep_frozen_set_step_once on page-locked host buffers: the kernels "
+                                        "read the input and write the output across the host link"}
     results["fma_peak_fp64"] = L.lmep_fma_peak("fp64")
     results["fma_peak_fp32"] = L.lmep_fma_peak("mixed")
     h.close()
@@ -1656,6 +1667,7 @@ def main():
                           "unit": "TFLOP/s", "frac": fp["f64"] / (fp["ms_per_step"] * 1e-3) / p64},
         "cpu_baseline": cpu,
         "e2e": res["e2e"],
+        "e2e_zero_copy": res["e2e_zero_copy"],
         "gpu_launches": 2 * args.steps,
         "clocks": m["clocks"],
         "clock_window": m["window"],

@@ -270,7 +270,11 @@ LMEP_API lmep_status lmep_frozen_set_refresh(lmep_handle* h, void* workspace_dev
  * non-overlapping buffers): two launches (the lean kernel, then the fallback
  * for the points it rejected, which returns at once when there are none), no
  * host synchronisation, suitable for replay in a CUDA graph that alternates
- * the two buffers.  Calls that share a workspace must not overlap on the GPU. */
+ * the two buffers.  Calls that share a workspace must not overlap on the GPU.
+ * u_in_dev and u_out_dev may also be page-locked host memory (cudaHostAlloc /
+ * cudaMallocHost) on a system with unified addressing: the kernels then read
+ * the input and write the output across the host link themselves, with no
+ * separate copy (same results, bit for bit). */
 LMEP_API lmep_status lmep_frozen_set_step_once(lmep_handle* h, const void* workspace_dev, const void* u_in_dev,
                                                void* u_out_dev, void* stream);
 

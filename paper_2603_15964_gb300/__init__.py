@@ -74,6 +74,14 @@ def _ptr(t) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+def _state_ptr(t) -> C.c_void_p:
+    """A state buffer: a contiguous CUDA tensor, or a contiguous pinned host tensor (read and written by the
+    kernels in place through unified addressing)."""
+    if not t.is_cuda and t.is_contiguous() and t.is_pinned():
+        return C.c_void_p(t.data_ptr())
+    return _ptr(t)
+
+
 def _stream(stream=None) -> C.c_void_p:
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -208,7 +216,9 @@ def lmep_frozen_set_refresh(h: Handle, workspace, stream=None) -> None:
 
 
 def lmep_frozen_set_step_once(h: Handle, workspace, u_in, u_out, stream=None) -> None:
-    _lib.call("lmep_frozen_set_step_once", h.ptr, _ptr(workspace), _ptr(u_in), _ptr(u_out), _stream(stream))
+    """One step of every instance of a prepared set, u_in -> u_out: CUDA tensors, or pinned host tensors."""
+    _lib.call("lmep_frozen_set_step_once", h.ptr, _ptr(workspace), _state_ptr(u_in), _state_ptr(u_out),
+              _stream(stream))
 
 
 def lmep_adjoint_scratch_bytes(grid: Grid, precision: str = "fp64") -> int:

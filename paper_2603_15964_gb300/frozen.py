@@ -176,7 +176,7 @@ def tune(instances, arrays, precision: str = "mixed", method: str = "auto", step
     """Time the fused step's launch shapes (threads per CTA, points per thread) on this GPU and return
     ((block, points_per_thread), {shape: ms per step}).  Each shape prepares its own workspace and is
     timed with CUDA events after two warm-up steps: over `steps` eager steps back to back, or with
-    cold=True as the median of `steps` lone steps, each after a 256 MiB write that evicts the L2 (a
+    cold=True as the mean of `steps` lone steps, each after a 256 MiB write that evicts the L2 (a
     step of a caller that does other work between steps).  The winner is cached per (GPU, instance
     widths and sizes, precision, route, timing) in $LMEP_AUTOTUNE_CACHE."""
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
@@ -211,7 +211,7 @@ def tune(instances, arrays, precision: str = "mixed", method: str = "auto", step
                 b.record()
                 b.synchronize()
                 lone.append(a.elapsed_time(b))
-            ms = sorted(lone)[len(lone) // 2]
+            ms = sum(lone) / len(lone)  # the mean: event times come in steps of about 1 us
         else:
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)

@@ -176,6 +176,28 @@ def test_set_graph_replay_without_rejections(L, precision):
     assert ctl == [0] * (len(probs) + 2), ctl
 
 
+@pytest.mark.parametrize("precision", PRECS)
+def test_set_step_with_pinned_host_buffers(L, precision):
+    # the step reads its input from, and writes its output to, page-locked host memory directly: the same
+    # bits as the step between device buffers (rejected points included: the fallback reads the host input)
+    probs = mixed_probs()
+    u0 = [ic_of(p, s) for s, p in enumerate(probs)]
+    fs = make_set(L, probs, precision)
+    fs.load(u0)
+    dev_in = fs.current().clone()
+    dev_out = torch.empty_like(dev_in)
+    L.lmep_frozen_set_step_once(fs.handle, fs.workspace, dev_in, dev_out)
+    host_in = dev_in.cpu().pin_memory()
+    host_out = torch.full_like(host_in, float("nan")).pin_memory()
+    L.lmep_frozen_set_step_once(fs.handle, fs.workspace, host_in, host_out)
+    torch.cuda.synchronize()
+    L.lmep_sync_status(fs.handle)
+    ref = dev_out.cpu()
+    offs = L.frozen_set_offsets([p.N for p in probs])
+    for o, p in zip(offs, probs):           # the padding between instances is neither read nor written
+        assert same_bits(host_out[o:o + p.N], ref[o:o + p.N])
+
+
 def test_set_refresh_is_idempotent(L):
     """Recomputing the exp(E) tables on the device gives the same steps."""
     probs = mixed_probs()[:3]
