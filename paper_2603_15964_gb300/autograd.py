@@ -19,7 +19,8 @@ from dataclasses import dataclass
 
 import torch
 
-from . import (Grid, Handle, Operator, lmep_adjoint_scratch_bytes, lmep_adjoint_step, lmep_step, state_dtype)
+from . import (Grid, Handle, Operator, lmep_adjoint_scratch_bytes, lmep_adjoint_step, lmep_frozen_set_prepare,
+               lmep_frozen_set_step_once, lmep_frozen_set_workspace_bytes, lmep_step, state_dtype)
 
 
 @dataclass
@@ -37,9 +38,14 @@ class FrozenVelocitySolver:
     bc_lo: float = 0.0
     bc_hi: float = 0.0
     handle: Handle | None = None
+    # step a batch as a frozen set (one persistent launch per step over all states; the same bits as
+    # lmep_step on the batched grid), prepared at first use for each (batch, nu) with the handle's expm
+    # route at that time; needs N % 4 == 0 (the set's packed layout is then the (batch, N) tensor)
+    use_set: bool = True
 
     def __post_init__(self):
         self.handle = self.handle or Handle()
+        self._sets = {}
 
     def grid(self, batch: int) -> Grid:
         return Grid(N=self.N, h=self.h, bc=self.bc, n=self.n, departure_centring=self.departure_centring,
@@ -48,11 +54,43 @@ class FrozenVelocitySolver:
     def op(self, nu: float) -> Operator:
         return Operator(c2=nu, frozen_adv=self.frozen_adv)
 
+    def _set_workspace(self, batch: int, nu: float) -> torch.Tensor:
+        key = (batch, nu)
+        if key not in self._sets:
+            if len(self._sets) >= 4:
+                self._sets.pop(next(iter(self._sets)))
+            g = [self.grid(1)] * batch
+            o = [self.op(nu)] * batch
+            t = [self.dt] * batch
+            ws = torch.empty(lmep_frozen_set_workspace_bytes(g, o, t, self.precision), dtype=torch.uint8,
+                             device="cuda")
+            lmep_frozen_set_prepare(self.handle, g, o, t, ws, self.precision)
+            self._sets[key] = ws
+        return self._sets[key]
+
     def advance(self, u: torch.Tensor, work: torch.Tensor, nu: float, nsteps: int) -> None:
         """nsteps forward steps of the whole batch in place (no autograd)."""
-        if nsteps > 0:
+        if nsteps <= 0:
+            return
+        if not (self.use_set and self.N % 4 == 0 and self.frozen_adv != 0.0):
             lmep_step(self.handle, self.grid(u.shape[0]), self.op(nu), "linear", "none", self.dt, None, u, work,
                       nsteps, self.precision)
+            return
+        ws = self._set_workspace(u.shape[0], nu)
+        src, dst = u, work
+        for _ in range(nsteps):
+            lmep_frozen_set_step_once(self.handle, ws, src, dst)
+            src, dst = dst, src
+        if src is not u:
+            u.copy_(src)
+
+    def step_into(self, src: torch.Tensor, dst: torch.Tensor, work: torch.Tensor, nu: float) -> None:
+        """One forward step of the whole batch from src into dst (src unchanged)."""
+        if self.use_set and self.N % 4 == 0 and self.frozen_adv != 0.0:
+            lmep_frozen_set_step_once(self.handle, self._set_workspace(src.shape[0], nu), src, dst)
+        else:
+            dst.copy_(src)
+            self.advance(dst, work, nu, 1)
 
     def __call__(self, u0: torch.Tensor, nu: torch.Tensor) -> torch.Tensor:
         return FrozenVelocitySolve.apply(u0, nu, self)
@@ -101,8 +139,8 @@ class FrozenVelocitySolve(torch.autograd.Function):
             length = min(K, solver.steps - seg * K)
             states = [ctx.checkpoints[seg]]
             for _ in range(length - 1):
-                nxt = states[-1].clone()
-                solver.advance(nxt, work, nu_v, 1)
+                nxt = torch.empty_like(states[-1])
+                solver.step_into(states[-1], nxt, work, nu_v)
                 states.append(nxt)
             for t in range(length - 1, -1, -1):
                 lmep_adjoint_step(solver.handle, grid, op, solver.dt, states[t], lam, lam_new, dnu, scratch,

@@ -146,3 +146,27 @@ def test_fp32_form_gradient_on_a_fine_grid(L):
     assert abs(d32 - d64) <= 1e-3 * abs(d64), (d32, d64)
     assert np.max(np.abs(g32 - g64)) <= 1e-3 * np.max(np.abs(g64))
     assert abs(n32 - n64) <= 1e-3 * abs(n64), (n32, n64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_set_forward_equals_batched_step(L, precision):
+    """The solver steps a batch as a frozen set (one launch per step over all states) or through lmep_step
+    on the batched grid: the same final states and gradients in u0, bit for bit (dJ/dnu to its
+    summation order)."""
+    from paper_2603_15964_gb300.autograd import FrozenVelocitySolver
+    p = wl.burgers(N=4096, n=9, cfl=2.0, nu=1e-5, steps=9, departure_centring=True)
+    dt_ = L.state_dtype(precision)
+    u0 = torch.tensor(np.stack([wl.burgers_ic(p.N, 20 + b) for b in range(3)]), dtype=dt_, device="cuda")
+    target = torch.tensor(np.stack([wl.burgers_ic(p.N, 40 + b) for b in range(3)]), device="cuda")
+    out = []
+    for use_set in (True, False):
+        solver = FrozenVelocitySolver(N=p.N, h=p.h, n=p.n, dt=p.dt, steps=p.steps, precision=precision,
+                                      checkpoint_every=4, use_set=use_set)
+        x = u0.clone().requires_grad_(True)
+        nu = torch.tensor(p.c2, dtype=torch.float64, requires_grad=True)
+        uT = solver(x, nu)
+        (0.5 * p.h * ((uT.double() - target) ** 2).sum()).backward()
+        out.append((uT.detach().clone(), x.grad.clone(), float(nu.grad)))
+    (a, ga, na), (b, gb, nb) = out
+    assert torch.equal(a, b) and torch.equal(ga, gb)
+    assert abs(na - nb) <= 1e-12 * abs(nb)      # dJ/dnu is summed with atomic adds: the order varies
