@@ -1410,6 +1410,8 @@ def profile_case(args) -> None:
                      (`-k regex:k_apply -s 3 -c 1`).
     rk4 [prec]       ETDRK4 on the viscous Burgers benchmark (N = 2^22, n = 13, FP32 by default): two
                      warm-up steps, then one (`-k regex:k_apply_rk4 -s 2 -c 1`).
+    kdv [prec]       configuration 4's KdV step (N = 2^20, n = 11, ETDRK2, FP32 by default): two warm-up
+                     steps, then one (`-k regex:k_apply -s 2 -c 1`).
     nodes [prec]     a stretched grid of 2^21 nodes (n = 9, Allen-Cahn ETD1, FP32 by default): the
                      per-node harvest, two warm-up steps, then one (`-k regex:k_apply_pw -s 2 -c 1`;
                      the harvest is the one k_warp launch)."""
@@ -1485,6 +1487,17 @@ def profile_case(args) -> None:
         L.lmep_harvest_scheme_weights(h, g, op, p.dt, "etdrk4", W, prec)
         u = torch.tensor(wl.burgers_etd_ic(p), dtype=L.state_dtype(prec), device="cuda")
         L.lmep_step(h, g, op, "etdrk4", "burgers", p.dt, W, u, torch.empty_like(u), 3, prec)
+        L.lmep_sync_status(h)
+    elif case == "kdv":
+        prec = rest[0] if rest else "mixed"
+        p = wl.kdv(N=1 << 20, n=11, steps=3)
+        g = L.Grid(N=p.N, h=p.h, bc=p.bc, n=p.n)
+        op = L.Operator(c3=p.c3)
+        h = L.Handle()
+        W = torch.empty(p.n, 3, p.n, dtype=L.state_dtype(prec), device="cuda")
+        L.lmep_harvest_weights(h, g, op, p.dt, 2, None, W, prec)
+        u = torch.tensor(wl.kdv_ic(p, 0), dtype=L.state_dtype(prec), device="cuda")
+        L.lmep_step(h, g, op, "etdrk2", "kdv", p.dt, W, u, torch.empty_like(u), 3, prec)
         L.lmep_sync_status(h)
     elif case == "nodes":
         from oracle import nodes as onodes

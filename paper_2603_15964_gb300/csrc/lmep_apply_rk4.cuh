@@ -30,14 +30,14 @@
 
 #include "lmep_device.cuh"
 #include "lmep_internal.h"
+#include "lmep_runs.cuh"
 
 namespace lmep {
 
 constexpr int RK4_ROWS = 6;                       // E, A, B, G, E2, P2 per row class
 constexpr int RK4_MAXW = DMAX * RK4_ROWS * DMAX;  // every row class (Dirichlet), width <= 16
-constexpr int RK4_RP = 9;  // consecutive points per thread and run (interior tiles; odd: the threads' windows
-                           // start 9 words apart, on 32 different banks)
-constexpr int RK4_PAD = RK4_RP + DMAX;            // slack after each staged field: a run's window may pass its end
+constexpr int RK4_RP = RUN_RP;    // consecutive points per thread and run (interior tiles)
+constexpr int RK4_PAD = RUN_PAD;  // slack after each staged field: a run's window may pass its end
 
 struct Rk4Params {
   int64_t N;
@@ -59,29 +59,6 @@ template <typename ST>
 struct Rk4Fields {
   ST *u, *Nu, *a, *Na, *b, *Nb, *c, *Nc;
 };
-
-// Row `row` of the centre class into registers.
-template <typename ST, int NW>
-__device__ __forceinline__ void rk4_row(const ST* src, ST (&w)[NW]) {
-#pragma unroll
-  for (int j = 0; j < NW; ++j) w[j] = src[j];
-}
-
-// A run's window: v[s .. s + RP + NW - 2] (inside the field and its slack).
-template <typename ST, int NW>
-__device__ __forceinline__ void rk4_window(const ST* v, int s, ST (&x)[RK4_RP + NW - 1]) {
-#pragma unroll
-  for (int j = 0; j < RK4_RP + NW - 1; ++j) x[j] = v[s + j];
-}
-
-// acc[p] += sum_j w[j] x[p + j], taps in order.
-template <typename ST, int NW>
-__device__ __forceinline__ void rk4_dot(const ST (&w)[NW], const ST (&x)[RK4_RP + NW - 1], ST (&acc)[RK4_RP]) {
-#pragma unroll
-  for (int p = 0; p < RK4_RP; ++p)
-#pragma unroll
-    for (int j = 0; j < NW; ++j) acc[p] = fma(w[j], x[p + j], acc[p]);
-}
 
 // ---- tiles next to a Dirichlet wall: per-point windows and row classes.
 template <typename ST, int NONLIN>
@@ -201,14 +178,14 @@ __device__ __forceinline__ void rk4_eval_fast(const ST* v, ST* dst, int lo, int 
     for (int q = lo + threadIdx.x; q < end; q += blockDim.x) dst[q] = nonlin_point<ST, 1>(v[q], ST(0), inv_h);
   } else {
     ST d[NW];
-    rk4_row<ST, NW>(d1row, d);
+    run_row<ST, NW>(d1row, d);
     for (int q0 = lo + int(threadIdx.x) * RK4_RP; q0 < end; q0 += int(blockDim.x) * RK4_RP) {
       ST x[RK4_RP + NW - 1];
-      rk4_window<ST, NW>(v, q0 - HS, x);
+      run_window<ST, NW>(v, q0 - HS, x);
       ST ux[RK4_RP];
 #pragma unroll
       for (int p = 0; p < RK4_RP; ++p) ux[p] = ST(0);
-      rk4_dot<ST, NW>(d, x, ux);
+      run_dot<ST, NW>(d, x, ux);
 #pragma unroll
       for (int p = 0; p < RK4_RP; ++p)
         if (q0 + p < end) dst[q0 + p] = nonlin_point<ST, NONLIN>(x[p + HS], ux[p], inv_h);
@@ -222,21 +199,21 @@ __device__ __forceinline__ void rk4_half_fast(const ST* x, const ST* y, ST* dst,
                                               const ST* p2row) {
   constexpr int HS = (NW - 1) / 2;
   ST e2[NW], p2[NW];
-  rk4_row<ST, NW>(e2row, e2);
-  rk4_row<ST, NW>(p2row, p2);
+  run_row<ST, NW>(e2row, e2);
+  run_row<ST, NW>(p2row, p2);
   for (int q0 = lo + int(threadIdx.x) * RK4_RP; q0 < end; q0 += int(blockDim.x) * RK4_RP) {
     ST acc[RK4_RP];
 #pragma unroll
     for (int p = 0; p < RK4_RP; ++p) acc[p] = ST(0);
     {
       ST w[RK4_RP + NW - 1];
-      rk4_window<ST, NW>(x, q0 - HS, w);
-      rk4_dot<ST, NW>(e2, w, acc);
+      run_window<ST, NW>(x, q0 - HS, w);
+      run_dot<ST, NW>(e2, w, acc);
     }
     {
       ST w[RK4_RP + NW - 1];
-      rk4_window<ST, NW>(y, q0 - HS, w);
-      rk4_dot<ST, NW>(p2, w, acc);
+      run_window<ST, NW>(y, q0 - HS, w);
+      run_dot<ST, NW>(p2, w, acc);
     }
 #pragma unroll
     for (int p = 0; p < RK4_RP; ++p)
@@ -291,10 +268,10 @@ __device__ void rk4_tile_fast(const Rk4Params& a, const Rk4Fields<ST>& f, const 
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         ST w[NW];
-        rk4_row<ST, NW>(rows + k * DMAX, w);
+        run_row<ST, NW>(rows + k * DMAX, w);
         ST x[RK4_RP + NW - 1];
-        rk4_window<ST, NW>(src[k], q0 - HS, x);
-        rk4_dot<ST, NW>(w, x, acc);
+        run_window<ST, NW>(src[k], q0 - HS, x);
+        run_dot<ST, NW>(w, x, acc);
       }
 #pragma unroll
       for (int p = 0; p < RK4_RP; ++p)

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(512) k_apply_stream(ApplyParams a, const ST* _
   const ST* ptab = static_cast<const ST*>(a.ptab);
   const T ZERO = PO::make(ST(0), ST(0));
   const T M1 = PO::make(ST(-1), ST(-1));
-  const ST inv_dt_s = ST(1.0 / a.dt);
+  const ST inv_dt_s = ST(a.inv_dt);
   const T INV = PO::make(inv_dt_s, inv_dt_s);
   T chk = ZERO;  // fma(out, 0, chk) turns any Inf/NaN output into NaN
   const int64_t nwarps = int64_t(gridDim.x) * (blockDim.x >> 5);

@@ -141,6 +141,10 @@ struct ApplyParams {
   int64_t N;
   double h;
   int bc;
+  // set by launch_apply: 1 / dt, 1 / h (one instance) and, for a derivative
+  // nonlinearity, the device table of h D^(1) rows of width n (row r at r * LD)
+  double inv_dt, inv_h;
+  const double* dh;
 };
 int apply_halo(int n, int scheme, int nonlin, int bc);
 int apply_fast_halo(int n, int scheme);
