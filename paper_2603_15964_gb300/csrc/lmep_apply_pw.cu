@@ -35,6 +35,7 @@ cudaError_t launch_apply_pw(int64_t N, int n, int scheme, int nonlin, double dt,
   PwParams a{};
   a.N = N;
   a.dt = dt;
+  a.inv_dt = 1.0 / dt;
   a.bc_lo = bc_lo;
   a.bc_hi = bc_hi;
   a.n = n;

@@ -10,6 +10,7 @@ namespace lmep {
 struct PwParams {
   int64_t N;
   double dt, bc_lo, bc_hi;
+  double inv_dt;  // 1 / dt, formed on the host
   int n, R, tile, halo;
   int64_t ntiles;
 };
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) k_apply_pw(PwParams a, const ST* __restri
   const int64_t N = a.N;
   const int R4 = 2 * hs;  // reach of a one-sided window
   const ST lo_v = ST(a.bc_lo), hi_v = ST(a.bc_hi);
-  const ST inv_dt = ST(1.0 / a.dt);
+  const ST inv_dt = ST(a.inv_dt);
   unsigned bad = 0;
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int64_t t0 = tile * int64_t(a.tile);

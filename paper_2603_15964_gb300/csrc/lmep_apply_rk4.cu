@@ -21,6 +21,7 @@ cudaError_t launch_apply_rk4(int64_t N, double h, int bc, int n, int nonlin, dou
   Rk4Params a{};
   a.N = N;
   a.h = h;
+  a.inv_h = 1.0 / h;
   a.dt = dt;
   a.bc_lo = bc_lo;
   a.bc_hi = bc_hi;

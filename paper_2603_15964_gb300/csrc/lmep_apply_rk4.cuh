@@ -42,6 +42,7 @@ constexpr int RK4_PAD = RUN_PAD;  // slack after each staged field: a run's wind
 struct Rk4Params {
   int64_t N;
   double h, dt, bc_lo, bc_hi;
+  double inv_h;     // 1 / h, formed on the host
   int n, bc, tile, halo;
   int rs, rN;       // reach of one stencil stage and of one N(.) evaluation
   int64_t ntiles;
@@ -68,7 +69,7 @@ __device__ void rk4_tile_generic(const Rk4Params& a, const Rk4Fields<ST>& f, con
   const int n = a.n, hs = (n - 1) >> 1, H = a.halo;
   const bool dir = a.bc == BC_DIRICHLET;
   const int64_t N = a.N;
-  const ST inv_h = ST(1.0 / a.h);
+  const ST inv_h = ST(a.inv_h);
   const ST lo_v = ST(a.bc_lo), hi_v = ST(a.bc_hi);
   // window of local point q: local start and harvest row
   auto window = [&](int q, int& ls, int& r) {
@@ -226,7 +227,7 @@ __device__ void rk4_tile_fast(const Rk4Params& a, const Rk4Fields<ST>& f, const 
                               int L, ST* __restrict__ out, unsigned& bad) {
   constexpr int HS = (NW - 1) / 2;
   const int H = a.halo, rs = a.rs, rN = a.rN;
-  const ST inv_h = ST(1.0 / a.h);
+  const ST inv_h = ST(a.inv_h);
   const ST* rows = sW + HS * RK4_ROWS * DMAX;  // centre class: E, A, B, G, E2, P2
   const ST* d1 = sD1 + HS * DMAX;
   int lo = rN;
