@@ -78,6 +78,23 @@ def test_shifted_windows_other_boundaries(L, H, precision, bc, shift, cfl):
     assert rel_linf(got, olmep.run(p, u0)) <= tol(precision) * p.steps
 
 
+@pytest.mark.parametrize("precision", PRECS)
+@pytest.mark.parametrize("bc,shift,cfl", [(wl.DIRICHLET, 3, 0.8), (wl.PERIODIC, 2, 2.4)])
+def test_shifted_windows_many_tiles(L, H, precision, bc, shift, cfl):
+    """As above on 9001 points: several tiles of the tiled kernel, interior ones included.  The
+    diffusion coefficient shrinks with h, so the local matrices (and the rows' l1 norms, which
+    bound the rounding the rows pass on) are those of the 1001-point grid."""
+    p = wl.Problem("adv", 9001, -1.0, 1.0, bc, 7, 0.0, c1=-0.7, c2=1e-4 / 9, window_shift=shift, steps=6)
+    p = p.with_(dt=cfl * p.h / 0.7)
+    u0 = np.sin(np.pi * p.nodes()) * np.exp(-p.nodes() ** 2)
+    if bc == wl.DIRICHLET:
+        u0[0] = u0[-1] = 0.0
+    if precision == "mixed":
+        u0 = u0.astype(np.float32).astype(np.float64)
+    got = run_gpu(L, H, p, u0, precision, p.steps)
+    assert rel_linf(got, olmep.run(p, u0)) <= tol(precision) * p.steps
+
+
 @pytest.mark.parametrize("one_sided", [True, False])
 def test_amplification_matches_oracle(L, H, one_sided):
     th = np.linspace(-np.pi, np.pi, 1001)

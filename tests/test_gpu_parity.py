@@ -206,6 +206,11 @@ def step_cases():
         "ac_etdrk2_n13_neumann": (wl.allen_cahn(2500, bc=wl.NEUMANN, n=13, scheme="etdrk2", steps=12), 7),
         "advdiff_n15_periodic": (wl.Problem("adv", 4099, -1.0, 1.0, wl.PERIODIC, 15, 0.0, c1=-1.0, c2=1e-4,
                                             steps=12).with_(dt=0.7 * 2.0 / 4099), None),
+        # walled grids of several tiles (2048 points in FP32, 1024 in FP64): the tiles whose halo stays clear
+        # of the walls take the interior path of the tiled kernel, the two next to the walls the per-point one
+        "dirichlet_advdiff_many_tiles": (wl.Problem("adv", 9001, 0.0, 1.0, wl.DIRICHLET, 7, 0.0, c1=-1.0, c2=1e-5,
+                                                    bc_lo=0.0, bc_hi=0.0, steps=12).with_(dt=2.2 / 9000), None),
+        "ac_etdrk2_dirichlet_tiles": (wl.allen_cahn(7001, bc=wl.DIRICHLET, n=9, scheme="etdrk2", steps=8, mu=0.1), 8),
     }
 
 
