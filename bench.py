@@ -69,9 +69,9 @@ P64_NOMINAL = 1.25e12                            # GB300 FP64 nominal
 #   frozen_set: one step of the nine-instance set (`--profile-case set 128 8`): the lean launch
 #     2,469,376 B and the fallback 72,192 B.
 #   apply_stream_ac: one step of the 4096-instance Allen-Cahn ETDRK2 batch (`--profile-case ac 1024 64`):
-#     253,727,232 B read + 197,143,808 B written.
+#     253,721,088 B read + 196,624,896 B written.
 TRAFFIC = {
-    "apply_stream_ac": (450_871_040, "163250995021b624",
+    "apply_stream_ac": (450_345_984, "9031e8300e201d2b",
                         ("lmep_apply_stream.cu", "lmep_stream.cuh", "lmep_device.cuh")),
     "frozen_set": (2_541_568, "de304222319da5ce",
                    ("lmep_frozen_set.cuh", "lmep_frozen_set.cu", "lmep_set_fb_f32.cu", "lmep_warp_kernel.cuh",
