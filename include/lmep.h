@@ -72,7 +72,11 @@ typedef enum { LMEP_EXPM_AUTO = 0, LMEP_EXPM_PADE = 1, LMEP_EXPM_SERIES = 2 } lm
  *         near a wall the window slides inside the domain (one-sided
  *         stencil, edge row).  Neumann: homogeneous, even reflection about the
  *         wall node.  Periodic: centred window, indices mod N.
- *  n      stencil width, odd, 3 <= n <= 15, n <= N.
+ *  n      stencil width, odd, 3 <= n <= 15, n <= N.  Wide stencils, odd
+ *         17 <= n <= 25 (the widths of the one-sided study of Sec. 4.1), are
+ *         built for the constant-coefficient linear scheme only: the harvest
+ *         with n_phi = 0 and the stored-weight step on a periodic grid, any
+ *         window_shift; every other call returns LMEP_ERR_UNSUPPORTED for them.
  *  departure_centring  frozen-velocity problems only: shift each window
  *         upstream by k_i = clamp(floor(u_i dt / h + 1/2), -(n-1)/2, (n-1)/2).
  *  batch  number of independent instances of this grid stored back to back
@@ -138,6 +142,10 @@ LMEP_API lmep_status lmep_expm(lmep_handle* h, const double* A_dev, int64_t P, i
  *  u_frozen_dev == NULL: constant coefficients; W_dev receives [n][1+n_phi][n]
  *      (0 <= n_phi <= 3, n + n_phi <= 16):
  *      W[r][k][:] = row r of dt^k phi_k(dt L) (k = 0: exp(dt L)) for every row class r.
+ *      Wide stencils (n = 17..25, n_phi = 0): the rows are formed in FP64 from
+ *      the factorisation row r of exp(X) = e^{c0 dt} l(r + a)^T exp(E)
+ *      (Thm. 1 and the General Exactness theorem; a = c1 dt / h, E = dt (c2 D2
+ *      + c3 D3) nilpotent, its exponential a finite Taylor sum), not by Pade.
  *  u_frozen_dev != NULL: frozen velocity (requires n_phi == 0): W_dev receives
  *      [batch][N][1][n], the weights of point i on its own window (zeros at Dirichlet walls).
  *      u_frozen_dev has the state dtype of `precision`.
@@ -171,6 +179,9 @@ LMEP_API lmep_status lmep_harvest_scheme_weights(lmep_handle* h, const lmep_grid
  *      N: lmep_nonlin, with D1 the harvest row of the first-derivative matrix
  *      on the same window.  KdV and Burgers terms with ETD1/ETDRK2 need a
  *      periodic grid; ETDRK4 takes every boundary condition.
+ *      Wide stencils (n = 17..25): the linear scheme on a periodic grid, with
+ *      the row of class (n-1)/2 + window_shift; other schemes and boundaries
+ *      return LMEP_ERR_UNSUPPORTED.
  *  W_dev == NULL: frozen velocity: every point rebuilds and exponentiates its
  *      own operator every step ((a1)-(a6) fused); requires the linear scheme.
  *  u_dev, work_dev: state dtype of `precision`, N elements each (batch * N for

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["lmep_set_fb_f64.cu", "lmep_set_fb_f32.cu", "lmep_expm_f64_hi.cu", "lmep_expm_f32_hi.cu",
            "lmep_frozen_set.cu", "lmep_expm_f64.cu", "lmep_expm_f32.cu", "lmep_adjoint.cu", "lmep_api.cu",
            "lmep_expm.cu", "lmep_apply.cu", "lmep_apply_f64.cu", "lmep_apply_stream.cu", "lmep_apply_rk4.cu", "lmep_apply_rk4_f64.cu", "lmep_apply_pw.cu", "lmep_apply_pw_f64.cu", "lmep_peak.cu", "lmep_noalloc.cu",
-           "lmep_spectral.cu"]
+           "lmep_spectral.cu", "lmep_wide.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden"]

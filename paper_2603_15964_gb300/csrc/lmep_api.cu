@@ -62,9 +62,24 @@ lmep_status cuda_fail(cudaError_t e, const char* where) {
 
 inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
 
-lmep_status check_grid(const lmep_grid* g, int n_phi) {
+// wide: the entry point also takes the wide stencils (odd n = 17 .. 25) of the
+// constant-coefficient linear scheme (lmep_wide.cu)
+lmep_status check_grid(const lmep_grid* g, int n_phi, bool wide = false) {
   if (!g) return fail(LMEP_ERR_INVALID, "grid is NULL");
-  if (g->n < 3 || g->n > 15 || (g->n % 2) == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15");
+  if (wide && n_phi == 0 && lmep::wide_width(g->n)) {
+    if (g->N < g->n) return fail(LMEP_ERR_INVALID, "N must be >= n");
+    if (g->N > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "N too large");
+    if (!(g->h > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
+    if (g->bc < 0 || g->bc > 2) return fail(LMEP_ERR_INVALID, "unknown boundary condition");
+    if (g->batch > 1) return fail(LMEP_ERR_UNSUPPORTED, "wide stencils take batch <= 1");
+    if (g->window_shift < -(g->n - 1) / 2 || g->window_shift > (g->n - 1) / 2)
+      return fail(LMEP_ERR_INVALID, "|window_shift| must be <= (n-1)/2");
+    if (g->reserved != 0) return fail(LMEP_ERR_INVALID, "lmep_grid.reserved must be 0");
+    return LMEP_OK;
+  }
+  if (lmep::wide_width(g->n))
+    return fail(LMEP_ERR_UNSUPPORTED, "n = 17..25 is built for the constant-coefficient linear scheme only");
+  if (g->n < 3 || g->n > 15 || (g->n % 2) == 0) return fail(LMEP_ERR_INVALID, "n must be odd, 3..15 (17..25: linear)");
   if (g->N < g->n) return fail(LMEP_ERR_INVALID, "N must be >= n");
   if (g->N > (int64_t(1) << 40)) return fail(LMEP_ERR_INVALID, "N too large");
   if (!(g->h > 0.0)) return fail(LMEP_ERR_INVALID, "h must be positive");
@@ -272,13 +287,20 @@ lmep_status lmep_harvest_weights(lmep_handle* h, const lmep_grid* g, const lmep_
                                  int32_t n_phi, const void* u_frozen_dev, void* W_dev, int32_t precision,
                                  void* stream) {
   if (!h || !op || !W_dev) return fail(LMEP_ERR_INVALID, "NULL handle/operator/W");
-  lmep_status st = check_grid(g, n_phi);
+  lmep_status st = check_grid(g, n_phi, true);
   if (st != LMEP_OK) return st;
   st = check_prec(precision);
   if (st != LMEP_OK) return st;
   if (!(dt > 0.0)) return fail(LMEP_ERR_INVALID, "dt must be positive");
   const KParams p = make_params(g, op, dt, n_phi);
   const bool mixed = precision == LMEP_PREC_MIXED;
+  if (g->n > 15) {
+    // wide stencils: constant coefficients, rows of exp(X) only (factorised form, lmep_wide.cu)
+    if (u_frozen_dev || op->frozen_adv != 0.0)
+      return fail(LMEP_ERR_UNSUPPORTED, "wide stencils (n > 15) take constant coefficients");
+    CK(lmep::launch_harvest_wide(p, W_dev, mixed, S(stream)), "harvest(wide)");
+    return LMEP_OK;
+  }
   if (u_frozen_dev) {
     if ((st = no_shift(g)) != LMEP_OK) return st;
     if (n_phi != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity weights need n_phi == 0");
@@ -332,7 +354,7 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
   if (scheme < 0 || scheme > 3) return fail(LMEP_ERR_INVALID, "unknown scheme");
   if (nonlin < 0 || nonlin > 3) return fail(LMEP_ERR_INVALID, "unknown nonlinearity");
   if ((scheme == 0) != (nonlin == 0)) return fail(LMEP_ERR_INVALID, "linear scheme <=> no nonlinearity");
-  lmep_status st = check_grid(g, scheme);
+  lmep_status st = check_grid(g, scheme, true);
   if (st != LMEP_OK) return st;
   st = check_prec(precision);
   if (st != LMEP_OK) return st;
@@ -345,6 +367,18 @@ lmep_status lmep_step(lmep_handle* h, const lmep_grid* g, const lmep_operator* o
   const size_t es = mixed ? 4 : 8;
   void* cur = u_dev;
   void* nxt = work_dev;
+  if (g->n > 15) {
+    // wide stencils: stored rows of the linear scheme on a periodic grid (lmep_wide.cu)
+    if (!W_dev || op->frozen_adv != 0.0) return fail(LMEP_ERR_UNSUPPORTED, "wide stencils (n > 15) take stored rows");
+    if (g->bc != LMEP_BC_PERIODIC) return fail(LMEP_ERR_UNSUPPORTED, "wide stencils (n > 15) step periodic grids");
+    for (int64_t t = 0; t < nsteps; ++t) {
+      CK(lmep::launch_apply_wide(g->N, g->n, g->window_shift, W_dev, cur, nxt, mixed, h->flags, S(stream)),
+         "step(wide)");
+      std::swap(cur, nxt);
+    }
+    if (cur != u_dev) CK(cudaMemcpyAsync(u_dev, cur, size_t(g->N) * es, cudaMemcpyDeviceToDevice, S(stream)), "copy");
+    return LMEP_OK;
+  }
   if (!W_dev) {
     if ((st = no_shift(g)) != LMEP_OK) return st;
     if (scheme != 0) return fail(LMEP_ERR_INVALID, "frozen-velocity stepping uses the linear scheme");

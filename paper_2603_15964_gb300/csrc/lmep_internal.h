@@ -47,6 +47,14 @@ void set_last_error(const std::string& msg);
 // parameters to the kernels.
 KParams make_params(const struct ::lmep_grid* g, const struct ::lmep_operator* op, double dt, int n_phi);
 
+// ---- wide stencils (lmep_wide.cu): odd n = 17 .. 25, constant-coefficient linear scheme
+bool wide_width(int n);
+// Rows W[r][0][j] of every row class r (FP64 arithmetic, stored in the state type).
+cudaError_t launch_harvest_wide(const KParams& p, void* W, bool mixed, cudaStream_t s);
+// One step u -> out on a periodic grid with the row of class (n - 1) / 2 + shift.
+cudaError_t launch_apply_wide(int64_t N, int n, int shift, const void* W, const void* u, void* out, bool mixed,
+                              unsigned* flags, cudaStream_t s);
+
 struct DeviceInfo {
   int sms;
   int smem_optin;  // dynamic shared memory a CTA may opt in to (bytes)
