@@ -5,7 +5,8 @@ constant-coefficient linear scheme, through the C ABI.
   the nilpotent local matrix of oracle.exact, no factorisation involved) within 1e-12 of its l1
   norm, the FP32 row within 1e-6.  For these widths the oracle's Pade of the rounded local matrix is
   itself off, by up to 1e-7 at n = 25 (the derivative matrices of wide windows have large norms), so
-  the exact rows decide, as they do for the FP64 rows of the nine-instance benchmark set.
+  the exact rows decide, as they do for the FP64 rows of the nine-instance benchmark set
+  (tests/test_readings_exact.py pins that gap, and the factorisation, at these widths).
 * One-sided advection for 100 periods (N = 256, nu = (n+1)/2 - 1/2): the GPU trajectory equals the
   oracle's banded step with the exact row within 1e-12 K (FP64) / 1e-5 K (FP32 form, 20 steps), and
   its error against the exact solution stays below 1e-7 (it grows at n = 25: the Runge onset the
@@ -126,15 +127,6 @@ def test_rows_equal_the_exact_rows(L, H, precision, n, case):
     for r in classes:
         want = exact_row(p, r)
         assert np.max(np.abs(W[r] - want)) <= bound * np.sum(np.abs(want)), r
-
-
-def test_oracle_pade_rows_are_themselves_off_at_wide_n():
-    """Why the exact rows decide: the oracle's Pade row of the diffusive n = 25 operator."""
-    p = general(25)
-    r = (p.n - 1) // 2
-    want = exact_row(p, r)
-    got = olmep.constant_weights(p)[r, 0]
-    assert np.max(np.abs(got - want)) > 1e-10 * np.sum(np.abs(want))
 
 
 # ------------------------------------------------------------------ trajectories

@@ -130,3 +130,53 @@ def test_series_error_within_two_u_beta(nu, n, cfl):
                 acc = acc + v
             err = np.max(np.abs(acc.astype(np.float64) - ex)) / np.sum(np.abs(ex))
             assert err <= 2.0 * unit * beta + 4 * unit, (i, dt_, err, beta)
+
+
+# ------------------------------------------------------------------ wide stencils (n = 17 .. 25)
+def row_series(n, X, v):
+    """v^T exp(X) for a nilpotent X, by the finite series of row-vector products."""
+    acc, t = v[:], v[:]
+    for k in range(1, n + 1):
+        t = [sum((t[i] * X[i][j] for i in range(n)), Fraction(0)) / k for j in range(n)]
+        if k == n:
+            assert all(x == 0 for x in t)
+            break
+        acc = [acc[j] + t[j] for j in range(n)]
+    return acc
+
+
+@pytest.mark.parametrize("n", [17, 25])
+def test_wide_derivative_matrices_are_powers(n):
+    """The wide rows take D2 = D1^2 and D3 = D1^3: exact on the window's polynomial space at these widths too."""
+    D1, D2, D3 = (exact.lagrange_D(range(n), k) for k in (1, 2, 3))
+    assert exact.matmul(D1, D1) == D2
+    assert exact.matmul(D2, D1) == D3
+
+
+@pytest.mark.parametrize("n", [17, 25])
+def test_wide_factorised_row_is_exact(n):
+    """Row r of exp(a D1 + b D2 + c D3) equals l(r + a)^T exp(b D2 + c D3) at the wide widths, for the
+    classes a one-sided (r = n - 1) and a centred (r = (n - 1) / 2) window take."""
+    D1, D2, D3 = (exact.lagrange_D(range(n), k) for k in (1, 2, 3))
+    a, b, c = Fraction(-n, 2), Fraction(1, 40), Fraction(-1, 900)
+    X = lin((a, D1), (b, D2), (c, D3))
+    E = lin((b, D2), (c, D3))
+    for r in (n - 1, (n - 1) // 2):
+        e_r = [Fraction(int(j == r)) for j in range(n)]
+        assert row_series(n, E, lagrange_row(n, r + a)) == row_series(n, X, e_r), r
+
+
+def test_oracle_pade_rows_are_themselves_off_at_wide_n():
+    """Why exact rows decide the GPU's wide rows: the oracle's Pade of the rounded local matrix of a
+    diffusive, dispersive n = 25 operator is off its exact row by more than 1e-10 of the row's l1 norm."""
+    from oracle import lmep as olmep
+    N = 3001
+    h = 2.0 / N
+    p = wl.Problem("adv", N, -1.0, 1.0, wl.PERIODIC, 25, 0.0, c0=-0.3, c1=-1.0, c2=0.0625 * h, c3=1e-3 * h * h,
+                   steps=1).with_(dt=0.8 * 2.0 / N)
+    r = 12
+    X = exact.local_matrix(p.n, p.dt, p.h, p.c1, p.c2, p.c3)
+    want = np.exp(p.c0 * p.dt) * np.array([float(x) for x in
+                                           row_series(p.n, X, [Fraction(int(j == r)) for j in range(p.n)])])
+    got = olmep.constant_weights(p)[r, 0]
+    assert np.max(np.abs(got - want)) > 1e-10 * np.sum(np.abs(want))
